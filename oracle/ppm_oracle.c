@@ -1,0 +1,451 @@
+/*
+ * ppm_oracle.c -- CPU oracle for hypothesis-tested progressive kernel
+ * estimation (FPPM / VCM+ merge path).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * statement of what the GPU path computes.  Only tests/, the smoke check in
+ * __graft_entry__ and the cpu_baseline / reference arm of bench.py may load
+ * it.  The product library never links or calls it, and it shares no code,
+ * header, table or constant generator with the CUDA sources.
+ *
+ * Precision: every statistic is FP64 (two-pass ANOVA over all m samples of a
+ * group, zeros included).  The per-pair geometric decisions (disk test,
+ * annulus, sector) are taken in a fixed FP32 operation sequence, because a
+ * floating-point comparison decides an integer there and both sides must
+ * take it in the same precision.  Compile with -ffp-contract=off: the only
+ * fused multiply-adds are the explicit fmaf() calls below.
+ *
+ * Paper: "Hypothesis Testing for Progressive Kernel Estimation and VCM
+ * Framework" (Lin, Hu, Jia, Li).  Each function cites the section or
+ * equation it restates.
+ *
+ * Parity pins (tests/test_oracle_pins.py): F critical values against closed
+ * forms (F(1,d)=t^2, F(2,d), F(d,2)), the chi-square limit 24.725/11 printed
+ * in Sec. 6.1.1 and scipy; the ANOVA F against scipy.stats.f_oneway on full
+ * sample tables and against the exact value F=1 for a single nonzero sample;
+ * classification against FP64 atan2 geometry and brute-force area fractions;
+ * the estimate against the analytic constant-irradiance plane; the rejection
+ * rate against alpha_F; the radius update against Eq. (radiusupdate).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_NA 2            /* equi-areal annuli, Sec. 6.1.1 */
+#define OR_NS 6            /* equi-areal sectors per annulus, Sec. 6.1.1 */
+#define OR_NG (OR_NA * OR_NS)
+
+/* ------------------------------------------------------------------------
+ * 1. F distribution (Sec. 3.2.2): the critical value F_c is the (1-alpha_F)
+ *    quantile of F(d1, d2) with d1 = n-1 and d2 = n(m-1).
+ *
+ *    CDF_F(f; d1, d2) = I_x(d1/2, d2/2), x = d1 f / (d1 f + d2), where I is
+ *    the regularized incomplete beta function.  I_x(a,b) is evaluated from
+ *    its continued fraction (Lentz's method), on the side of the symmetry
+ *    I_x(a,b) = 1 - I_{1-x}(b,a) where the fraction converges fast.  The
+ *    log-Beta prefactor is taken in long double because lgamma(b) and
+ *    lgamma(a+b) are ~1e10 at the sample sizes of this method.  The quantile
+ *    is found by plain bisection on the monotone CDF.
+ * ---------------------------------------------------------------------- */
+static double or_beta_cf(double a, double b, double x)
+{
+    const double tiny = 1e-300;
+    double c = 1.0, d = 1.0 - (a + b) * x / (a + 1.0), h;
+    if (fabs(d) < tiny) d = tiny;
+    d = 1.0 / d;
+    h = d;
+    for (int k = 1; k < 100000; ++k) {
+        double num, delta;
+        /* even step: d_{2k} = k (b-k) x / ((a+2k-1)(a+2k)) */
+        num = k * (b - k) * x / ((a + 2.0 * k - 1.0) * (a + 2.0 * k));
+        d = 1.0 + num * d; if (fabs(d) < tiny) d = tiny;
+        c = 1.0 + num / c; if (fabs(c) < tiny) c = tiny;
+        d = 1.0 / d;
+        h *= d * c;
+        /* odd step: d_{2k+1} = -(a+k)(a+b+k) x / ((a+2k)(a+2k+1)) */
+        num = -(a + k) * (a + b + k) * x / ((a + 2.0 * k) * (a + 2.0 * k + 1.0));
+        d = 1.0 + num * d; if (fabs(d) < tiny) d = tiny;
+        c = 1.0 + num / c; if (fabs(c) < tiny) c = tiny;
+        d = 1.0 / d;
+        delta = d * c;
+        h *= delta;
+        if (fabs(delta - 1.0) < 1e-16) break;
+    }
+    return h;
+}
+
+double oracle_betainc(double a, double b, double x)
+{
+    if (x <= 0.0) return 0.0;
+    if (x >= 1.0) return 1.0;
+    long double lnB = lgammal((long double)a) + lgammal((long double)b)
+                    - lgammal((long double)a + (long double)b);
+    long double lnpre = (long double)a * logl((long double)x)
+                      + (long double)b * log1pl(-(long double)x) - lnB;
+    double pre = (double)expl(lnpre);
+    if (x < (a + 1.0) / (a + b + 2.0))
+        return pre * or_beta_cf(a, b, x) / a;
+    return 1.0 - pre * or_beta_cf(b, a, 1.0 - x) / b;
+}
+
+double oracle_f_cdf(double d1, double d2, double f)
+{
+    if (f <= 0.0) return 0.0;
+    double x = d1 * f / (d1 * f + d2);
+    return oracle_betainc(0.5 * d1, 0.5 * d2, x);
+}
+
+double oracle_f_crit(double d1, double d2, double alpha)
+{
+    double target = 1.0 - alpha, lo = 0.0, hi = 1.0;
+    while (oracle_f_cdf(d1, d2, hi) < target) { lo = hi; hi *= 2.0; }
+    for (int it = 0; it < 2000; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (oracle_f_cdf(d1, d2, mid) < target) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+/* ------------------------------------------------------------------------
+ * 2. One-way ANOVA F statistic, Eq. (f-statistic), two passes, FP64.
+ *    Group g holds m samples: the c_g stored values vals[off_g .. off_g+c_g)
+ *    plus m - c_g implicit zeros (Sec. 3.2.1: one light sub-path gives one
+ *    sample to every sector; the sectors it does not reach get a zero).
+ *    Returns F; *ssw_out receives the within-group sum of squares.
+ * ---------------------------------------------------------------------- */
+double oracle_anova_f(int n, double m, const int64_t* counts,
+                      const double* vals, double* ssw_out)
+{
+    double total = 0.0, mean_g[64], ssb = 0.0, ssw = 0.0;
+    int64_t off = 0;
+    if (n > 64) return -1.0;
+    /* pass 1: group means and grand mean over all n*m samples */
+    for (int g = 0; g < n; ++g) {
+        double s = 0.0;
+        for (int64_t j = 0; j < counts[g]; ++j) s += vals[off + j];
+        mean_g[g] = s / m;
+        total += s;
+        off += counts[g];
+    }
+    double grand = total / (n * m);
+    /* pass 2: deviations */
+    off = 0;
+    for (int g = 0; g < n; ++g) {
+        double dev = mean_g[g] - grand;
+        ssb += m * dev * dev;
+        for (int64_t j = 0; j < counts[g]; ++j) {
+            double e = vals[off + j] - mean_g[g];
+            ssw += e * e;
+        }
+        ssw += (m - (double)counts[g]) * mean_g[g] * mean_g[g];
+        off += counts[g];
+    }
+    if (ssw_out) *ssw_out = ssw;
+    if (ssw <= 0.0) return 0.0;
+    return (ssb / (n - 1)) / (ssw / (n * (m - 1.0)));
+}
+
+/* ------------------------------------------------------------------------
+ * 3. Per-pair classification in the unified 2D space.
+ *    - same-surface filter (the paper is silent; standard photon-mapping
+ *      normal check): integer dot of the two snorm8-packed normals > 8064,
+ *      i.e. cosine > ~1/2; skipped when either side has no normals;
+ *    - disk test (kernel support, Eq. kaplanyan-integral): closed disk,
+ *      d2 = fma(dz,dz, fma(dy,dy, dx*dx)) <= r*r, dx = x_h - x_p;
+ *    - map to the unified space, Eq. (map-function):
+ *      y_u = <x_h - x_p, u>, y_v = <x_h - x_p, v>;
+ *    - two equi-areal annuli (Sec. 3.2.1 / 6.1.1): inner iff 2 rho^2 < r^2;
+ *    - six equi-areal 60-degree sectors by exact sign logic against
+ *      sqrt(3) = 1.7320508f (tan 60 degrees).
+ *    Returns the group 0..11 (annulus * 6 + sector) or -1 if not gathered.
+ * ---------------------------------------------------------------------- */
+static int or_s8(uint32_t q, int byte)
+{
+    int v = (int)((q >> (8 * byte)) & 0xffu);
+    return v >= 128 ? v - 256 : v;
+}
+
+int oracle_normal_dot(uint32_t a, uint32_t b)
+{
+    return or_s8(a, 0) * or_s8(b, 0) + or_s8(a, 1) * or_s8(b, 1)
+         + or_s8(a, 2) * or_s8(b, 2) + or_s8(a, 3) * or_s8(b, 3);
+}
+
+int oracle_classify(const float* xh, const float* u, const float* v,
+                    float r, const float* xp,
+                    int use_normals, uint32_t nq_h, uint32_t nq_p)
+{
+    if (use_normals && oracle_normal_dot(nq_h, nq_p) <= 8064) return -1;
+    float dx = xh[0] - xp[0], dy = xh[1] - xp[1], dz = xh[2] - xp[2];
+    float r2 = r * r;
+    float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    if (!(d2 <= r2)) return -1;
+    float yu = fmaf(dz, u[2], fmaf(dy, u[1], dx * u[0]));
+    float yv = fmaf(dz, v[2], fmaf(dy, v[1], dx * v[0]));
+    float rho2 = fmaf(yv, yv, yu * yu);
+    int ring = ((rho2 + rho2) < r2) ? 0 : 1;
+    float ax = fabsf(yu), ay = fabsf(yv);
+    float tx = 1.7320508f * ax;
+    int up = (yv > 0.0f) || (yv == 0.0f && yu >= 0.0f);
+    int sector;
+    if (ay >= tx) sector = up ? 1 : 4;
+    else if (up)  sector = (yu > 0.0f) ? 0 : 2;
+    else          sector = (yu < 0.0f) ? 3 : 5;
+    return ring * OR_NS + sector;
+}
+
+/* ------------------------------------------------------------------------
+ * 4. Radius update, Eq. (radiusupdate): after iteration i, a rejected radius
+ *    becomes max(k r_i, r_min sqrt((i+1)^(alpha-1))).  The bound is a
+ *    per-iteration scalar, evaluated in FP64 and rounded to FP32; the radius
+ *    itself is FP32 state.
+ * ---------------------------------------------------------------------- */
+float oracle_radius_bound(float r_min, float alpha, int i)
+{
+    return (float)((double)r_min * sqrt(pow((double)i + 1.0, (double)alpha - 1.0)));
+}
+
+float oracle_shrink(float r, float k, float bound)
+{
+    float kr = k * r;
+    return kr > bound ? kr : bound;
+}
+
+/* ------------------------------------------------------------------------
+ * 5. VCM+ merge weight, balance heuristic (beta = 1), Eq. (mis-weight):
+ *    dividing numerator and denominator by n_VM p_VM of the technique that
+ *    produced the pair gives w = 1 / (1 + R_VM + R_VC / eta) with
+ *    eta = n_VM pi r^2 (p_VM is proportional to r^2, p_VC independent of r).
+ *    R_VM = rho_vm_h cos_l / pi + rho_vm_l (other merge techniques),
+ *    R_VC = rho_vc_h + rho_vc_l (connection techniques), cos_l = max(0,
+ *    n_h . w_l) from the snorm8-packed incoming direction of the light
+ *    vertex.  The rho are synthetic r-independent pdf ratios given as input.
+ * ---------------------------------------------------------------------- */
+double oracle_mis_weight(double rho_vm_h, double rho_vc_h, double rho_vm_l,
+                         double rho_vc_l, int cos_dot, double n_vm, double r)
+{
+    double cosl = cos_dot > 0 ? (double)cos_dot / (127.0 * 127.0) : 0.0;
+    double r_vm = rho_vm_h * cosl / M_PI + rho_vm_l;
+    double r_vc = rho_vc_h + rho_vc_l;
+    double eta = n_vm * M_PI * r * r;
+    return 1.0 / (1.0 + r_vm + r_vc / eta);
+}
+
+/* Luminance of an RGB flux (Rec. 709 weights; the paper tests luminance by
+ * default, Sec. 5.1, without stating the weights). */
+static double or_lum(double R, double G, double B)
+{
+    return 0.2126 * R + 0.7152 * G + 0.0722 * B;
+}
+
+/* ------------------------------------------------------------------------
+ * 6. The full method, brute force over all pairs (Sec. 5.1, steps 1-5, with
+ *    the estimate of Eq. progressive-VCM-estimator).  For every iteration
+ *    i = i0 .. i0+iters-1 and every hit point h:
+ *      a. classify every photon of the iteration (section 3 above);
+ *      b. append (group, psi) of each gathered photon to the window of h;
+ *         psi = luminance (or one RGB channel) of w * Phi;
+ *      c. tau_h += sum(w * Phi) / (pi r^2) with the radius of this iteration;
+ *      d. m = t' J with t' = t+1 iterations in the window; two-pass ANOVA F
+ *         per tested channel; F_c from d2 = 12 (m - 1); reject iff F > F_c
+ *         (any channel in RGB mode);
+ *      e. reject: shrink r, clear the window, t = 0; else t = t'.
+ *    Hit points are independent given the photons, so the loop over hit
+ *    points is a plain parallel-for.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    float k;          /* shrinking ratio */
+    float alpha;      /* radius-bound exponent */
+    float r_min;      /* lower-bound scale r_min (absolute) */
+    float n_vm;       /* light sub-paths used for merging (VCM+) */
+    double alpha_f;   /* significance level of the F-test */
+    int32_t rgb_test; /* 1: F-test on R, G and B, reject if any rejects */
+    int32_t vcm;      /* 1: weight each sample by the VCM+ merge weight */
+    int32_t i0;       /* global index of the first iteration (1-based) */
+    int32_t pad;
+} oracle_params;
+
+typedef struct {
+    int32_t n, cap;
+    int8_t* grp;
+    double* val;      /* nch values per entry */
+} or_window;
+
+static void or_push(or_window* w, int nch, int g, const double* v)
+{
+    if (w->n == w->cap) {
+        int cap = w->cap ? 2 * w->cap : 256;
+        w->grp = (int8_t*)realloc(w->grp, (size_t)cap);
+        w->val = (double*)realloc(w->val, (size_t)cap * nch * sizeof(double));
+        w->cap = cap;
+    }
+    w->grp[w->n] = (int8_t)g;
+    for (int c = 0; c < nch; ++c) w->val[(size_t)w->n * nch + c] = v[c];
+    w->n++;
+}
+
+/* F for one channel of a window: regroup the stored values by group. */
+static double or_window_f(const or_window* w, int nch, int ch, double m,
+                          int64_t* counts_out, double* sums_out, double* sq_out)
+{
+    int64_t counts[OR_NG] = {0};
+    for (int j = 0; j < w->n; ++j) counts[w->grp[j]]++;
+    double* vals = (double*)malloc(sizeof(double) * (size_t)(w->n > 0 ? w->n : 1));
+    int64_t off[OR_NG], fill[OR_NG];
+    int64_t o = 0;
+    for (int g = 0; g < OR_NG; ++g) { off[g] = o; fill[g] = 0; o += counts[g]; }
+    for (int j = 0; j < w->n; ++j) {
+        int g = w->grp[j];
+        vals[off[g] + fill[g]++] = w->val[(size_t)j * nch + ch];
+    }
+    if (counts_out) for (int g = 0; g < OR_NG; ++g) counts_out[g] = counts[g];
+    if (sums_out || sq_out) {
+        for (int g = 0; g < OR_NG; ++g) {
+            double s = 0.0, q = 0.0;
+            for (int64_t j = 0; j < counts[g]; ++j) {
+                s += vals[off[g] + j];
+                q += vals[off[g] + j] * vals[off[g] + j];
+            }
+            if (sums_out) sums_out[g] = s;
+            if (sq_out) sq_out[g] = q;
+        }
+    }
+    double F = oracle_anova_f(OR_NG, m, counts, vals, NULL);
+    free(vals);
+    return F;
+}
+
+/*
+ * Inputs (all host arrays, row-major):
+ *   hp_pos, hp_u, hp_v: nh*3 float; hp_nq: nh packed snorm8 normals or NULL;
+ *   hp_rho: nh*2 float (rho_vm_h, rho_vc_h) for VCM+, else NULL;
+ *   r_init: nh float initial radii (windows start empty, t = 0);
+ *   ph_pos: iters*J*3 float; ph_flux: iters*J*nch float (nch = 1 or 3);
+ *   ph_nq: iters*J packed normals or NULL; ph_rho: iters*J*2 float
+ *   (rho_vm_l, rho_vc_l) and ph_wq: iters*J packed directions, VCM+ only.
+ * Outputs (each may be NULL):
+ *   out_r:      (iters+1)*nh  radius used in each iteration, then final radius
+ *   out_counts: iters*nh*12   window counts c_g that the test of that
+ *                             iteration used (after accumulation, before reset)
+ *   out_S:      iters*nh*12   window sums of psi (test channel 0) per group
+ *   out_Q:      iters*nh*12   window sums of psi^2 per group
+ *   out_F:      iters*nh      F of test channel 0
+ *   out_Fc:     iters*nh      critical value used
+ *   out_reject: iters*nh      1 if rejected
+ *   out_pairs:  iters*nh      in-disk pairs gathered in that iteration
+ *   out_t:      nh            final window length t
+ *   out_tau:    nh*nch        final accumulated estimate sum
+ * Returns 0 on success, -1 on bad arguments.
+ */
+int oracle_run(int64_t nh, const float* hp_pos, const float* hp_u,
+               const float* hp_v, const uint32_t* hp_nq, const float* hp_rho,
+               const float* r_init, int iters, int64_t J, const float* ph_pos,
+               const float* ph_flux, int nch, const uint32_t* ph_nq,
+               const float* ph_rho, const uint32_t* ph_wq,
+               const oracle_params* prm,
+               float* out_r, int32_t* out_counts, double* out_S,
+               double* out_Q, double* out_F, double* out_Fc,
+               uint8_t* out_reject, int32_t* out_pairs, int32_t* out_t,
+               double* out_tau)
+{
+    if (nh < 0 || iters < 0 || J < 2 || (nch != 1 && nch != 3) || !prm)
+        return -1;
+    if (prm->vcm && (!hp_rho || !ph_rho || !ph_wq || !hp_nq)) return -1;
+    const int use_normals = (hp_nq != NULL && ph_nq != NULL);
+    const int ntest = (prm->rgb_test && nch == 3) ? 3 : 1;
+    const int wch = ntest;   /* values stored per window entry */
+
+    /* critical values for every window length t' that can occur */
+    int tmax = iters;
+    double* fc = (double*)malloc(sizeof(double) * (size_t)(tmax + 1));
+    for (int t = 1; t <= tmax; ++t)
+        fc[t] = oracle_f_crit(OR_NG - 1, OR_NG * ((double)t * (double)J - 1.0), prm->alpha_f);
+    float* bound = (float*)malloc(sizeof(float) * (size_t)(iters > 0 ? iters : 1));
+    for (int it = 0; it < iters; ++it)
+        bound[it] = oracle_radius_bound(prm->r_min, prm->alpha, prm->i0 + it);
+
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t h = 0; h < nh; ++h) {
+        const float* xh = hp_pos + 3 * h;
+        const float* u = hp_u + 3 * h;
+        const float* v = hp_v + 3 * h;
+        float r = r_init[h];
+        int32_t t = 0;
+        double tau[3] = {0.0, 0.0, 0.0};
+        or_window win = {0, 0, NULL, NULL};
+        for (int it = 0; it < iters; ++it) {
+            const float* P = ph_pos + (size_t)it * J * 3;
+            const float* PHI = ph_flux + (size_t)it * J * nch;
+            if (out_r) out_r[(size_t)it * nh + h] = r;
+            double phi_sum[3] = {0.0, 0.0, 0.0};
+            int32_t pairs = 0;
+            for (int64_t p = 0; p < J; ++p) {
+                size_t gp = (size_t)it * J + p;
+                int g = oracle_classify(xh, u, v, r, P + 3 * p, use_normals,
+                                        use_normals ? hp_nq[h] : 0,
+                                        use_normals ? ph_nq[gp] : 0);
+                if (g < 0) continue;
+                pairs++;
+                double w = 1.0;
+                if (prm->vcm) {
+                    int cd = oracle_normal_dot(hp_nq[h], ph_wq[gp]);
+                    w = oracle_mis_weight(hp_rho[2 * h], hp_rho[2 * h + 1],
+                                          ph_rho[2 * gp], ph_rho[2 * gp + 1],
+                                          cd, prm->n_vm, (double)r);
+                }
+                double phi[3], val[3];
+                for (int c = 0; c < nch; ++c) {
+                    phi[c] = w * (double)PHI[(size_t)p * nch + c];
+                    phi_sum[c] += phi[c];
+                }
+                if (ntest == 3) { val[0] = phi[0]; val[1] = phi[1]; val[2] = phi[2]; }
+                else if (nch == 3) val[0] = or_lum(phi[0], phi[1], phi[2]);
+                else val[0] = phi[0];
+                or_push(&win, wch, g, val);
+            }
+            /* Eq. (progressive-VCM-estimator): kernel estimate of iteration
+             * i with its own radius r_i; 1/(pi r^2) is the normalized disk
+             * kernel. */
+            double area = M_PI * (double)r * (double)r;
+            for (int c = 0; c < nch; ++c) tau[c] += phi_sum[c] / area;
+
+            int32_t tp = t + 1;
+            double m = (double)tp * (double)J;
+            int reject = 0;
+            double F0 = 0.0;
+            int64_t cnt[OR_NG];
+            double S[OR_NG], Q[OR_NG];
+            for (int ch = 0; ch < ntest; ++ch) {
+                double F = or_window_f(&win, wch, ch, m, ch == 0 ? cnt : NULL,
+                                       ch == 0 ? S : NULL, ch == 0 ? Q : NULL);
+                if (ch == 0) F0 = F;
+                if (F > fc[tp]) reject = 1;
+            }
+            size_t o = (size_t)it * nh + h;
+            if (out_counts) for (int g = 0; g < OR_NG; ++g) out_counts[o * OR_NG + g] = (int32_t)cnt[g];
+            if (out_S) for (int g = 0; g < OR_NG; ++g) out_S[o * OR_NG + g] = S[g];
+            if (out_Q) for (int g = 0; g < OR_NG; ++g) out_Q[o * OR_NG + g] = Q[g];
+            if (out_F) out_F[o] = F0;
+            if (out_Fc) out_Fc[o] = fc[tp];
+            if (out_reject) out_reject[o] = (uint8_t)reject;
+            if (out_pairs) out_pairs[o] = pairs;
+            if (reject) {
+                r = oracle_shrink(r, prm->k, bound[it]);
+                win.n = 0;
+                t = 0;
+            } else {
+                t = tp;
+            }
+        }
+        if (out_r) out_r[(size_t)iters * nh + h] = r;
+        if (out_t) out_t[h] = t;
+        if (out_tau) for (int c = 0; c < nch; ++c) out_tau[h * nch + c] = tau[c];
+        free(win.grp);
+        free(win.val);
+    }
+    free(fc);
+    free(bound);
+    return 0;
+}
