@@ -1,0 +1,384 @@
+"""Benchmark of the hypothesis-tested progressive kernel estimation path.
+
+A step is one iteration of the method over one batch of photons: build the
+photon grid (cell key, stable radix sort, cell ranges, permute) and gather /
+F-test / update every hit point.  Default workload: the frame-sized plain
+configuration -- 1920x1080 hit points on the three faces z=0, y=0, x=0 of the
+unit box, 2,000,000 photons per iteration (uniform density + 2 anisotropic
+Gaussian caustic lobes + 2 step-edge shadows), r0 = 0.01, 64 iterations in
+total (warm-up + timed).  Metric: in-disk photon/hit-point pair tests per
+second (pairs gathered by the gather's disk test), whole job.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "photon-hitpoint pair tests/sec"
+UNIT = "pairs/s"
+
+# algorithmic bytes of the gather kernel (k_gather_update), per unit
+GATHER_BYTES_PER_PHOTON = 16 + 4          # sorted record + aux word (normals), read once
+GATHER_BYTES_PER_HIT = 48 + 4 + 4 + 8 + 144 + (4 + 4 + 8 + 4 + 144)
+# static record read; r, t, tau, window (12 x count/S/Q) read; r, t, tau, F, window written
+# algorithmic FP32/INT ops of the canonical per-pair sequence
+OPS_PER_CANDIDATE = 7     # 3 sub, 1 mul + 2 fma (d^2), 1 compare
+OPS_PER_PAIR = 28         # normal dp4a+cmp 2, map 6, rho^2 2, ring 2, sector 9, group 1, accumulate 4, flux 2
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def _src_hash(path):
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def _profile_traffic(config):
+    """dram bytes per gather launch from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    ent = d.get(config)
+    if not ent:
+        return None
+    if ent.get("src_sha") != _src_hash(os.path.join(ROOT, "paper_2504_04411_gb300", "csrc", "ppm_gather.cu")):
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    def __init__(self, dev_index=0):
+        self.dev = dev_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}",
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                rows.append((float(f[0]), float(f[1]), f[4:8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+# ----------------------------------------------------------------- oracle --
+def oracle_sample(scene, batches_np, hp_np, n_hits, seed=0):
+    """Run the CPU oracle (as it stands) over one iteration for a random
+    subset of hit points; returns (pairs, seconds, threads)."""
+    import numpy as np
+
+    from oracle import oracle as O
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(hp_np["pos"].shape[0], n_hits, replace=False))
+    sub = {k: v[idx] for k, v in hp_np.items()}
+    t0 = time.perf_counter()
+    res = O.run(sub, batches_np, scene.r0, 1, outputs=True)
+    dt = time.perf_counter() - t0
+    return int(res.pairs.sum()), dt
+
+
+def cpu_baseline(scene, hp_np, ph_np, budget_s=12.0):
+    threads = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(threads))
+    probe = 128
+    pairs, dt = oracle_sample(scene, ph_np, hp_np, probe, seed=1)
+    n = int(min(hp_np["pos"].shape[0], max(probe, probe * budget_s / max(dt, 1e-3))))
+    pairs, dt = oracle_sample(scene, ph_np, hp_np, n, seed=2)
+    return {"value": pairs / dt, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", threads)),
+            "kind": "oracle",
+            "sample": f"{n} random hit points of the workload x 1 iteration of {ph_np['pos'].shape[1]} "
+                      f"photons, brute force all pairs, FP64 statistics, {dt:.1f} s"}
+
+
+# ------------------------------------------------------------------ main ---
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=61)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="frame", choices=["frame", "tiny"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-flush", action="store_true")
+    return ap.parse_args()
+
+
+def make_scene(config, rank):
+    from paper_2504_04411_gb300 import synth
+    if config == "tiny":
+        sc = synth.PlaneScene(nside=64, J=100_000, r0=0.02, step=True, seed=synth.SEED_BASE + 1000 * rank)
+        desc = {"workload": "plain, tiny: 64x64 hit points on z=0, 100k photons/iter, step edge, r0=0.02",
+                "hit_points": 4096, "photons_per_iter": 100_000, "r0": 0.02}
+    else:
+        sc = synth.BoxScene(seed=synth.SEED_BASE + 1 + 1000 * rank)
+        desc = {"workload": "plain, frame-sized: 1920x1080 hit points on 3 faces of the unit box, "
+                            "2M photons/iter (uniform + 2 Gaussian caustic lobes + 2 step-edge shadows), r0=0.01",
+                "hit_points": sc.nh, "photons_per_iter": sc.J, "r0": sc.r0}
+    return sc, desc
+
+
+def main():
+    args = parse()
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = world > 1
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        return run_reference(args)
+    torch.cuda.set_device(local)
+    if dist:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if dist:
+        tdist.barrier()
+    __graft_entry__.build()
+    from paper_2504_04411_gb300 import ppm, synth
+
+    sc, desc = make_scene(args.config, rank)
+    W, K = args.warmup, args.steps
+    hp = sc.hitpoints("cuda")
+    batches = [sc.photons(i, "cuda") for i in range(1, W + K + 1)]
+    torch.cuda.synchronize()
+    flush = None if args.no_flush else torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    stream = torch.cuda.current_stream()
+    est = ppm.Estimator(hp, sc.r0, 0.75)
+    for i in range(W):
+        est.step(batches[i])
+    torch.cuda.synchronize()
+    st0 = est.stats()
+    pairs0 = st0.pairs_total
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    cand = 0
+    launches = 0
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(K):
+        if flush is not None:
+            flush.zero_()                     # evict L2 between steps (not timed)
+        a, b, c = ev[i]
+        ph = batches[W + i]
+        a.record(stream)
+        ppm.ppm_build_grid(est.ctx, ph.pos, ph.flux, ph.pos.shape[0], nq=ph.nq)
+        b.record(stream)
+        est.it += 1
+        ppm.ppm_gather_test_update(est.ctx, est.it)
+        c.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        tdist.barrier()
+    clk = clocks.stop()
+    st = est.stats()
+    pairs = st.pairs_total - pairs0
+    launches = st.launches * K
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    gather_ms = [b.elapsed_time(c) for a, b, c in ev]
+    build_ms = [a.elapsed_time(b) for a, b, c in ev]
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s, float(pairs)], device="cuda", dtype=torch.float64)
+        tmax = t[:1].clone()
+        tdist.all_reduce(tmax, op=tdist.ReduceOp.MAX)
+        tsum = t[1:].clone()
+        tdist.all_reduce(tsum, op=tdist.ReduceOp.SUM)
+        total_s, all_pairs = float(tmax), float(tsum)
+    else:
+        all_pairs = float(pairs)
+    value = all_pairs / total_s
+
+    # ---- roofline of the dominant kernel (the gather) ----------------------
+    peaks = _peaks()
+    g_s = statistics.mean(gather_ms) / 1e3
+    bytes_launch = sc.J * GATHER_BYTES_PER_PHOTON + hp.n * GATHER_BYTES_PER_HIT
+    hbm_achieved = bytes_launch / g_s / 1e9
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    ops_launch = (st.candidates * OPS_PER_CANDIDATE + st.pairs * OPS_PER_PAIR)
+    sm_count = torch.cuda.get_device_properties(0).multi_processor_count
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = sm_count * 128 * sm_mhz * 1e6 / 1e12      # Tops/s (FP32 lanes x clock)
+    alu_achieved = ops_launch / g_s / 1e12
+    hbm = {"bound": "hbm", "achieved": round(hbm_achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+           "frac": round(hbm_achieved / hbm_peak, 4), "traffic": _profile_traffic(args.config),
+           "algorithmic_bytes": bytes_launch, "kernel": "k_gather_update",
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"}
+    alu = {"bound": "alu", "achieved": round(alu_achieved, 3), "peak": round(alu_peak, 2), "unit": "Tops/s",
+           "frac": round(alu_achieved / alu_peak, 4), "traffic": hbm["traffic"],
+           "algorithmic_ops": ops_launch, "kernel": "k_gather_update",
+           "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz"}
+    roof, other = (alu, hbm) if alu["frac"] >= hbm["frac"] else (hbm, alu)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": 1e3 * total_s / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(desc, l2="flushed between steps (256 MB write, untimed)" if flush is not None else "not flushed",
+                           parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                           iterations_total=W + K),
+            "iterations_per_sec": K / total_s,
+            "candidates_per_sec": st.candidates * K / total_s if False else None,
+            "build_ms": statistics.mean(build_ms), "gather_ms": statistics.mean(gather_ms),
+            "wall_s": wall, "gpu_launches": launches,
+            "roofline": roof, "roofline_other": other, "clocks": clk}
+    line["candidates_last_iter"] = st.candidates
+    line["pairs_last_iter"] = st.pairs
+    line["rejects_last_iter"] = st.rejects
+
+    # ---- end to end through the public API with host buffers -------------
+    if not args.no_e2e:
+        e2e = run_e2e(est, batches, W, K, stream, sc)
+        if dist:
+            t = torch.tensor([e2e["seconds"], float(e2e["pairs"])], device="cuda", dtype=torch.float64)
+            tm = t[:1].clone(); tdist.all_reduce(tm, op=tdist.ReduceOp.MAX)
+            ts = t[1:].clone(); tdist.all_reduce(ts, op=tdist.ReduceOp.SUM)
+            e2e["seconds"], e2e["pairs"] = float(tm), float(ts)
+        line["e2e"] = {"value": e2e["pairs"] / e2e["seconds"], "unit": UNIT,
+                       "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]}
+    est.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        hp_np = hp.numpy()
+        ph_np = synth.stack_numpy([batches[W]])
+        del batches
+        line["cpu_baseline"] = cpu_baseline(sc, hp_np, ph_np)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        tdist.destroy_process_group()
+    return 0
+
+
+def run_e2e(est, batches, W, K, stream, sc):
+    """The same iterations through the public API with host-resident inputs:
+    each step copies its photons from pinned host memory, runs the
+    iteration, and reads the iteration's counters back."""
+    import torch
+
+    from paper_2504_04411_gb300 import ppm
+    host = []
+    for i in range(K):
+        ph = batches[W + i]
+        host.append((ph.pos.cpu().pin_memory(), ph.flux.cpu().pin_memory(), ph.nq.cpu().pin_memory()))
+    h2d = sum(t.numel() * t.element_size() for t in host[0])
+    # continue the same estimator: the sequence stays valid
+    torch.cuda.synchronize()
+    pairs = 0
+    t0 = time.perf_counter()
+    for i in range(K):
+        pos, flux, nq = (t.to("cuda", non_blocking=True) for t in host[i])
+        ppm.ppm_build_grid(est.ctx, pos, flux, pos.shape[0], nq=nq)
+        est.it += 1
+        ppm.ppm_gather_test_update(est.ctx, est.it)
+        s = ppm.ppm_stats(est.ctx)        # waits; reads the iteration's counters back
+        pairs += s.pairs
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"pairs": pairs, "seconds": dt, "h2d": h2d, "d2h": 56}
+
+
+def run_reference(args):
+    """The oracle as it stands on the host cores, on the same config, one
+    bounded sample of hit points per step against the step's photons."""
+    import numpy as np
+
+    from paper_2504_04411_gb300 import synth
+    sc, desc = make_scene(args.config, 0)
+    hp_np = sc.hitpoints("cpu").numpy()
+    threads = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(threads))
+    W, K = args.warmup, args.steps
+    # size the per-step sample so that the whole run stays within minutes
+    ph_np = synth.stack_numpy([sc.photons(1, "cpu")])
+    _, dt = oracle_sample(sc, ph_np, hp_np, 64, seed=0)
+    per_step_s = min(2.0, 150.0 / (W + K))
+    n = int(min(hp_np["pos"].shape[0], max(16, 64 * per_step_s / max(dt, 1e-3))))
+    pairs = 0
+    secs = 0.0
+    for i in range(W + K):
+        ph_np = synth.stack_numpy([sc.photons(i + 1, "cpu")])
+        p, dt = oracle_sample(sc, ph_np, hp_np, n, seed=100 + i)
+        if i >= W:
+            pairs += p
+            secs += dt
+    value = pairs / secs
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+            "steps": K, "warmup": W, "ms_per_step": 1e3 * secs / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(desc, l2="n/a (CPU)", parallelism="host cores"),
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
+                             "kind": "oracle",
+                             "sample": f"per step {n} random hit points x 1 iteration of {sc.J} photons, "
+                                       f"brute force all pairs, FP64 statistics"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

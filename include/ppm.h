@@ -1,0 +1,196 @@
+/*
+ * ppm.h -- C ABI of libppm: hypothesis-tested progressive kernel estimation
+ * (FPPM, and the VM part of VCM+) on one GB300 (sm_103a).
+ *
+ * Method: "Hypothesis Testing for Progressive Kernel Estimation and VCM
+ * Framework" (Lin, Hu, Jia, Li).  Every iteration i the caller hands in the
+ * iteration's photons (light vertices); the library
+ *   1. builds a hashed uniform grid over them (cell key + stable LSD radix
+ *      sort + cell ranges) -- the range-search structure of Sec. 5.1;
+ *   2. gathers, for every hit point, the photons inside its disk of radius
+ *      r_i, maps them into the unified 2D space of Eq. (map-function), and
+ *      accumulates per group (2 equi-areal annuli x 6 sectors, Sec. 3.2.1 /
+ *      6.1.1) the count, the sum of psi and the sum of psi^2 (Sec. 5.1 step 2);
+ *   3. evaluates the ANOVA F statistic of Eq. (f-statistic) with m = t*J
+ *      samples per group (Sec. 3.2.1, 5.1), compares it with the critical
+ *      value F_c of F(11, 12(m-1)) at significance alpha_F (Sec. 3.2.2), and
+ *      applies Eq. (radiusupdate); the window of samples is kept while the
+ *      radius is kept and cleared when it shrinks (Sec. 5.1);
+ *   4. accumulates the progressive estimate of Eq. (progressive-VCM-estimator):
+ *      tau += Phi_i / (pi r_i^2).  For VCM+ every gathered pair carries the
+ *      balance-heuristic merge weight of Eq. (mis-weight) (Sec. 4.2).
+ *
+ * Conventions (all entry points):
+ *   - Return PPM_OK (0) or a negative PPM_E* code; ppm_strerror() names it.
+ *   - Pointers in ppm_hitpoints / ppm_photons and output pointers are DEVICE
+ *     pointers on the current CUDA device, borrowed for the duration of the
+ *     work the call enqueues (stream-ordered); the library never frees them.
+ *   - All work is enqueued on the stream given to ppm_create (or
+ *     ppm_set_stream).  No entry point synchronizes the host except
+ *     ppm_create, ppm_stats, ppm_get_state/ppm_set_state (which wait for
+ *     their own copies) and ppm_destroy.
+ *   - Floating-point layouts are row-major: an "n x 3" array holds x,y,z of
+ *     element 0, then of element 1, ...
+ *   - Packed directions ("snorm8") are uint32 words holding four signed
+ *     bytes (x | y<<8 | z<<16 | 0<<24), each round(127 * component).
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef PPM_H
+#define PPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PPM_OK        0
+#define PPM_EINVAL   (-1)   /* bad argument (NULL, size, layout, range) */
+#define PPM_ENOMEM   (-2)   /* device allocation failed */
+#define PPM_ECUDA    (-3)   /* a CUDA runtime call or launch failed */
+#define PPM_ETIMEOUT (-4)   /* a bounded device-side wait gave up */
+#define PPM_ESTATE   (-5)   /* call out of order (iteration sequence) */
+
+#define PPM_NGROUPS 12      /* 2 annuli x 6 sectors, Sec. 6.1.1 */
+
+typedef struct ppm_ctx ppm_ctx;  /* opaque; owned by the library */
+
+/* Hit points (eye vertices / gather points, Sec. 3.1), fixed for the life of
+ * a context.  pos, u, v: n x 3 float; (u, v) is an orthonormal tangent frame
+ * of Eq. (map-function).  nq: n packed snorm8 surface normals, or NULL for a
+ * single-surface scene (no same-surface filter).  rho: n x 2 float
+ * (rho_vm_h, rho_vc_h), the eye-side pdf ratios of the VCM+ merge weight;
+ * required iff params->vcm. */
+typedef struct {
+    int64_t n;
+    const float* pos;
+    const float* u;
+    const float* v;
+    const uint32_t* nq;
+    const float* rho;
+} ppm_hitpoints;
+
+/* Photons (light vertices) of one iteration.  pos: n x 3 float.  flux: n
+ * float (channels = 1) or n x 3 float RGB (channels = 3).  J: light
+ * sub-paths emitted this iteration = samples per group per iteration
+ * (Sec. 3.2.1); must be >= 2 and the same in every iteration of a context.
+ * nq: n packed snorm8 normals, or NULL (then the hit points' normals are
+ * ignored too).  VCM+ only: rho n x 2 float (rho_vm_l, rho_vc_l) and wq n
+ * packed incoming directions. */
+typedef struct {
+    int64_t n;
+    int64_t J;
+    const float* pos;
+    const float* flux;
+    int32_t channels;
+    int32_t pad;
+    const uint32_t* nq;
+    const float* rho;
+    const uint32_t* wq;
+} ppm_photons;
+
+/* Method parameters.  ppm_default_params() fills the paper's defaults. */
+typedef struct {
+    float k;            /* shrinking ratio of Eq. (radiusupdate), 0.7 (Sec. 6.1.1) */
+    float alpha_f;      /* significance level alpha_F, 0.01 (Sec. 6.1.1) */
+    float rmin_ratio;   /* r_min = rmin_ratio * r0, 0.001 (Sec. 6.1.2) */
+    float cell_factor;  /* grid cell edge = cell_factor * max radius, in [0.5, 4]; 1 */
+    int32_t channels;   /* flux channels of every iteration: 1 or 3 */
+    int32_t rgb_test;   /* 0: F-test on luminance (default); 1: one F-test per
+                           RGB channel, reject if any rejects (Sec. 5.1) */
+    int32_t vcm;        /* 1: weight samples by the VCM+ merge weight */
+    float n_vm;         /* VCM+: light sub-paths used for merging; 0 = J */
+    int32_t mapping;    /* gather mapping: 0 = default (thread per hit point) */
+    int32_t reserved[7];
+} ppm_params;
+
+/* Per-iteration counters of the last ppm_gather_test_update. */
+typedef struct {
+    int32_t iter;          /* last completed iteration (0 = none) */
+    int32_t flags;         /* device error flags; bit 0: a sphere spanned more
+                              cells than a hash block (results incomplete);
+                              bit 1: a window length outside the F_c table
+                              (from ppm_set_state), clamped */
+    int64_t pairs;         /* in-disk photon/hit-point pairs gathered */
+    int64_t candidates;    /* photons visited in the scanned cells */
+    int64_t rejects;       /* hit points whose null hypothesis was rejected */
+    int64_t pairs_total;   /* pairs summed over all iterations */
+    float r_max;           /* largest radius after the update */
+    float cell;            /* grid cell edge used by the last build */
+    int32_t launches;      /* kernels launched by the last build + gather */
+    int32_t pad;
+} ppm_iter_stats;
+
+/* State per hit point, in the caller's hit-point order (device pointers;
+ * any may be NULL to skip it).  ntc = 3 if rgb_test else 1.
+ *   r: n float radius; t: n int32 iterations in the current window;
+ *   counts: n x 12 int32 in-disk photons per group in the window;
+ *   S, Q: n x ntc x 12 float window sums of psi and psi^2 per group;
+ *   tau: n x channels double accumulated estimate sum; F: n float F of the
+ *   last test (luminance / channel 0). */
+typedef struct {
+    float* r;
+    int32_t* t;
+    int32_t* counts;
+    float* S;
+    float* Q;
+    double* tau;
+    float* F;
+} ppm_state_view;
+
+void ppm_default_params(ppm_params* p);
+
+/* Create a context over n hit points with initial radius r0 > 0 for all of
+ * them and radius-bound exponent alpha in (0,1) (Eq. radiusupdate; 0.75 in
+ * Sec. 6.1.2).  params may be NULL (defaults).  stream is a cudaStream_t (or
+ * NULL for the legacy default stream).  Copies the hit points into a
+ * spatially sorted internal layout; the caller may free its arrays once the
+ * call returns.  Synchronizes the stream once.  *out is NULL on error. */
+int ppm_create(const ppm_hitpoints* hp, float r0, float alpha,
+               const ppm_params* params, void* stream, ppm_ctx** out);
+
+/* Change the stream later work is enqueued on. */
+int ppm_set_stream(ppm_ctx* ctx, void* stream);
+
+/* Step 1 of an iteration (Sec. 5.1: build the range-search structure):
+ * hash every photon to a grid cell of edge cell_factor * max_h r_h, sort
+ * (cell, index) pairs with a stable radix sort, and copy the photons into
+ * cell order.  The photon arrays may be reused once the stream passes this
+ * work.  n = 0 is allowed (an iteration without photons). */
+int ppm_build_grid(ppm_ctx* ctx, const ppm_photons* ph);
+
+/* Steps 2-4 of iteration iter (Sec. 5.1 steps 2-4 and Eq. progressive-VCM-
+ * estimator) over the grid of the last ppm_build_grid.  iter must be the
+ * previous iteration + 1, starting at 1, with a grid built since
+ * (PPM_ESTATE otherwise). */
+int ppm_gather_test_update(ppm_ctx* ctx, int32_t iter);
+
+/* Radiance estimate L = tau / iter (Eq. progressive-VCM-estimator) into out:
+ * n float (channels = 1) or n x 3 float, device, caller's hit-point order. */
+int ppm_radiance(ppm_ctx* ctx, float* out);
+
+/* Copy the state out of / into the context (checkpoint / resume, tests).
+ * Both wait for the copies to finish.  set_state leaves the iteration
+ * counter untouched; use ppm_set_iteration to resume a sequence. */
+int ppm_get_state(ppm_ctx* ctx, const ppm_state_view* v);
+int ppm_set_state(ppm_ctx* ctx, const ppm_state_view* v);
+int ppm_set_iteration(ppm_ctx* ctx, int32_t iter);
+
+/* Counters of the last iteration; waits for the stream. */
+int ppm_stats(ppm_ctx* ctx, ppm_iter_stats* out);
+
+/* F-test critical values on their own (Sec. 3.2.2): out[t] = the
+ * (1 - alpha_f) quantile of F(11, 12 (t J - 1)) for t = 1 .. t_max, FP64,
+ * out[0] = 0.  out: device array of t_max + 1 doubles.  Enqueued on stream. */
+int ppm_f_critical(int64_t J, float alpha_f, int32_t t_max, double* out, void* stream);
+
+/* Frees everything the context owns (waits for the stream first). */
+void ppm_destroy(ppm_ctx* ctx);
+
+const char* ppm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PPM_H */

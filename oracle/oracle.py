@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 import sys
 from dataclasses import dataclass
@@ -32,6 +33,8 @@ def build(force: bool = False) -> str:
     tmp = _LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
            "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    if platform.machine() in ("x86_64", "AMD64"):
+        cmd.append("-lquadmath")   # binary128 log-gamma (long double is binary128 on aarch64)
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB

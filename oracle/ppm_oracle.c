@@ -42,12 +42,31 @@
  *
  *    CDF_F(f; d1, d2) = I_x(d1/2, d2/2), x = d1 f / (d1 f + d2), where I is
  *    the regularized incomplete beta function.  I_x(a,b) is evaluated from
- *    its continued fraction (Lentz's method), on the side of the symmetry
- *    I_x(a,b) = 1 - I_{1-x}(b,a) where the fraction converges fast.  The
- *    log-Beta prefactor is taken in long double because lgamma(b) and
- *    lgamma(a+b) are ~1e10 at the sample sizes of this method.  The quantile
- *    is found by plain bisection on the monotone CDF.
+ *    its continued fraction (Lentz's method).  Of the two sides of the
+ *    symmetry I_x(a,b) = 1 - I_{1-x}(b,a) the fraction is evaluated on the
+ *    one where it converges fast (x < (a+1)/(a+b+2)), except when b >> a:
+ *    there the other side's odd terms are -1 + O(1/b) and every step cancels
+ *    ~9 digits, while the direct side stays well conditioned and converges
+ *    in a few dozen terms.  The log-Beta prefactor is taken in quadruple
+ *    precision (binary128: long double on aarch64, __float128 on x86-64)
+ *    because lgamma(b) and lgamma(a+b) are ~1e11 at the sample sizes of
+ *    this method.  The quantile is found by plain bisection on the CDF.
  * ---------------------------------------------------------------------- */
+#if defined(__x86_64__)
+#include <quadmath.h>
+typedef __float128 or_quad;
+#define OR_LGAMMA lgammaq
+#define OR_LOG logq
+#define OR_LOG1P log1pq
+#define OR_EXP expq
+#else
+typedef long double or_quad;
+#define OR_LGAMMA lgammal
+#define OR_LOG logl
+#define OR_LOG1P log1pl
+#define OR_EXP expl
+#endif
+
 static double or_beta_cf(double a, double b, double x)
 {
     const double tiny = 1e-300;
@@ -79,12 +98,12 @@ double oracle_betainc(double a, double b, double x)
 {
     if (x <= 0.0) return 0.0;
     if (x >= 1.0) return 1.0;
-    long double lnB = lgammal((long double)a) + lgammal((long double)b)
-                    - lgammal((long double)a + (long double)b);
-    long double lnpre = (long double)a * logl((long double)x)
-                      + (long double)b * log1pl(-(long double)x) - lnB;
-    double pre = (double)expl(lnpre);
-    if (x < (a + 1.0) / (a + b + 2.0))
+    or_quad lnB = OR_LGAMMA((or_quad)a) + OR_LGAMMA((or_quad)b)
+                - OR_LGAMMA((or_quad)a + (or_quad)b);
+    or_quad lnpre = (or_quad)a * OR_LOG((or_quad)x)
+                  + (or_quad)b * OR_LOG1P(-(or_quad)x) - lnB;
+    double pre = (double)OR_EXP(lnpre);
+    if (x < (a + 1.0) / (a + b + 2.0) || b > 50.0 * a)
         return pre * or_beta_cf(a, b, x) / a;
     return 1.0 - pre * or_beta_cf(b, a, 1.0 - x) / b;
 }

@@ -1,0 +1,121 @@
+// ppm_fcrit.cu -- table of F-test critical values, FP64 on the GPU.
+//
+// Sec. 3.2.2: reject the null hypothesis iff F > F_c, where F_c is the
+// (1 - alpha_F) quantile of the F distribution with d1 = n - 1 = 11 and
+// d2 = n (m - 1) degrees of freedom; Sec. 6.1.1 updates F_c at run time with
+// the sample count.  With m = t J samples per group (t iterations in the
+// window, J light paths per iteration) the table is indexed by t.
+//
+// CDF_F(f) = I_x(d1/2, d2/2) with x = d1 f / (d1 f + d2) (regularized
+// incomplete beta).  I is evaluated from its continued fraction with the
+// modified Lentz method, on the side of I_x(a,b) = 1 - I_{1-x}(b,a) where
+// the fraction converges quickly -- except for b >> a (d2 >> d1, always the
+// case here), where the other side's odd terms are -1 + O(1/b) and each
+// step cancels ~9 digits: there the direct side is well conditioned and
+// converges in a few dozen terms.  The quantile is found by Newton's
+// method on the CDF (derivative = the F density) kept inside a bisection
+// bracket.  d2 reaches ~1e11, where lgamma(b) - lgamma(a+b) loses ~1e-6 to
+// cancellation in FP64, so for large b that difference is taken from the
+// Stirling series of log Gamma written as a difference (no cancellation).
+#include "ppm_internal.cuh"
+
+namespace {
+
+__device__ double lbeta_fp64(double a, double b)
+{
+    if (b < 1.0e4) return lgamma(a) + lgamma(b) - lgamma(a + b);
+    // log G(b) - log G(a+b) from log G(z) = (z-1/2) log z - z + log(2 pi)/2
+    //   + 1/(12 z) - 1/(360 z^3) + 1/(1260 z^5) - ...
+    const double ab = a + b;
+    double d = -(b - 0.5) * log1p(a / b) - a * log(ab) + a;
+    const double ib = 1.0 / b, iab = 1.0 / ab;
+    const double ib3 = ib * ib * ib, iab3 = iab * iab * iab;
+    d += (ib - iab) / 12.0 - (ib3 - iab3) / 360.0 + (ib3 * ib * ib - iab3 * iab * iab) / 1260.0;
+    return lgamma(a) + d;
+}
+
+// continued fraction of I_x(a,b) (without the x^a (1-x)^b / (a B) factor)
+__device__ double betacf_fp64(double a, double b, double x)
+{
+    const double fpmin = 1e-300;
+    double c = 1.0;
+    double d = 1.0 - (a + b) * x / (a + 1.0);
+    if (fabs(d) < fpmin) d = fpmin;
+    d = 1.0 / d;
+    double h = d;
+    for (int m = 1; m <= 4000; ++m) {
+        const double m2 = 2.0 * m;
+        double aa = m * (b - m) * x / ((a - 1.0 + m2) * (a + m2));
+        d = 1.0 + aa * d; if (fabs(d) < fpmin) d = fpmin;
+        c = 1.0 + aa / c; if (fabs(c) < fpmin) c = fpmin;
+        d = 1.0 / d;
+        h *= d * c;
+        aa = -(a + m) * (a + b + m) * x / ((a + m2) * (a + 1.0 + m2));
+        d = 1.0 + aa * d; if (fabs(d) < fpmin) d = fpmin;
+        c = 1.0 + aa / c; if (fabs(c) < fpmin) c = fpmin;
+        d = 1.0 / d;
+        const double del = d * c;
+        h *= del;
+        if (fabs(del - 1.0) < 2e-16) break;
+    }
+    return h;
+}
+
+// CDF and density of F(d1, d2) at f > 0
+__device__ void f_cdf_pdf(double d1, double d2, double f, double* cdf, double* pdf)
+{
+    const double a = 0.5 * d1, b = 0.5 * d2;
+    const double s = d1 * f;
+    const double x = s / (s + d2);
+    const double lx = log(x);
+    const double l1x = -log1p(s / d2);          // log(1 - x) without cancellation
+    const double lb = lbeta_fp64(a, b);
+    const double front = exp(a * lx + b * l1x - lb);
+    if (x < (a + 1.0) / (a + b + 2.0) || b > 50.0 * a) *cdf = front * betacf_fp64(a, b, x) / a;
+    else *cdf = 1.0 - front * betacf_fp64(b, a, d2 / (s + d2)) / b;
+    // d/df I_x = x^(a-1) (1-x)^(b-1) / B(a,b) * dx/df, dx/df = d1 d2 / (s + d2)^2
+    *pdf = exp((a - 1.0) * lx + (b - 1.0) * l1x - lb) * d1 * d2 / ((s + d2) * (s + d2));
+}
+
+__device__ double f_quantile(double d1, double d2, double q)
+{
+    double lo = 0.0, hi = 4.0, c, p;
+    for (int i = 0; i < 200; ++i) {             // bracket the root
+        f_cdf_pdf(d1, d2, hi, &c, &p);
+        if (c >= q) break;
+        lo = hi;
+        hi *= 2.0;
+    }
+    double f = 0.5 * (lo + hi);
+    for (int it = 0; it < 100; ++it) {
+        f_cdf_pdf(d1, d2, f, &c, &p);
+        const double g = c - q;
+        if (g < 0.0) lo = f; else hi = f;
+        double fn = (p > 0.0) ? f - g / p : 0.5 * (lo + hi);
+        if (!(fn > lo && fn < hi)) fn = 0.5 * (lo + hi);   // keep Newton in the bracket
+        if (fabs(fn - f) <= 1e-15 * f || hi - lo <= 1e-15 * hi) { f = fn; break; }
+        f = fn;
+    }
+    return f;
+}
+
+__global__ void k_fcrit_table(double* __restrict__ table, int t_from, int t_to,
+                              double J, double alpha)
+{
+    const int t = t_from + blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > t_to) return;
+    const double m = (double)t * J;                  // samples per group
+    const double d1 = PPM_NG - 1, d2 = PPM_NG * (m - 1.0);
+    table[t] = f_quantile(d1, d2, 1.0 - alpha);
+}
+
+}  // namespace
+
+int ppm_fcrit_fill(double* table, int t_from, int t_to, double J, double alpha, cudaStream_t st)
+{
+    if (t_to < t_from) return PPM_OK;
+    const int n = t_to - t_from + 1;
+    k_fcrit_table<<<(n + 63) / 64, 64, 0, st>>>(table, t_from, t_to, J, alpha);
+    PPM_LAUNCH_CHECK();
+    return PPM_OK;
+}

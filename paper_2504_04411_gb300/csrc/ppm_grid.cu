@@ -1,0 +1,196 @@
+// ppm_grid.cu -- photon map of one iteration (Sec. 5.1: "build a range
+// search data structure of the light vertices"): a hashed uniform grid.
+//
+//   k_grid_geom  : cell edge h = cell_factor * max_h r_h, read from device
+//                  memory written by the previous update (no host sync);
+//   k_pack_keys  : one coalesced pass over the caller's photons: bucket key,
+//                  identity index, and the photon packed into 16-byte records;
+//   radix sort   : stable, on the bucket bits (ppm_sort.cu);
+//   k_cell_start : cell_start[b] = first sorted photon with bucket >= b;
+//   k_permute    : packed records gathered into bucket order.
+#include "ppm_internal.cuh"
+
+namespace {
+
+__global__ void k_grid_geom(GridGeom* __restrict__ g, const float* __restrict__ rmax,
+                            float cell_factor, uint32_t tmask, int lb)
+{
+    float r = *rmax;
+    if (!(r > 0.f)) r = 1e-30f;
+    const float h = __fmul_rn(cell_factor, r);
+    GridGeom o;
+    o.h = h;
+    o.inv_h = __frcp_rn(h);
+    o.tmask = tmask;
+    o.lb = lb;
+    *g = o;
+}
+
+// Rec. 709 luminance of an RGB flux (the paper tests luminance, Sec. 5.1).
+__device__ __forceinline__ float lum709(float R, float G, float B)
+{
+    return fmaf(0.0722f, B, fmaf(0.7152f, G, __fmul_rn(0.2126f, R)));
+}
+
+template <int NCH, bool AUX, bool VCM>
+__global__ void __launch_bounds__(256)
+k_pack_keys(int64_t n, const float* __restrict__ pos, const float* __restrict__ flux,
+            const uint32_t* __restrict__ nq, const float* __restrict__ rho,
+            const uint32_t* __restrict__ wq, const GridGeom* __restrict__ geom,
+            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+            float4* __restrict__ pack0, float4* __restrict__ pack1, uint4* __restrict__ pack_aux)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const GridGeom g = *geom;
+    const float x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+    float R, G = 0.f, B = 0.f, psi;
+    if (NCH == 3) {
+        R = flux[3 * i]; G = flux[3 * i + 1]; B = flux[3 * i + 2];
+        psi = lum709(R, G, B);
+    } else {
+        R = flux[i];
+        psi = R;
+    }
+    pack0[i] = make_float4(x, y, z, psi);
+    if (NCH == 3 || VCM)
+        pack1[i] = make_float4(R, G, B, VCM ? rho[2 * i] : 0.f);
+    if (AUX)
+        pack_aux[i] = make_uint4(nq ? nq[i] : 0u, VCM ? wq[i] : 0u,
+                                 VCM ? __float_as_uint(rho[2 * i + 1]) : 0u, 0u);
+    const int ix = ppm_cell_coord(x, g.inv_h);
+    const int iy = ppm_cell_coord(y, g.inv_h);
+    const int iz = ppm_cell_coord(z, g.inv_h);
+    keys[i] = ppm_bucket(ix, iy, iz, g);
+    vals[i] = (uint32_t)i;
+}
+
+// One thread per sorted photon i in [0, n]: fills the buckets between the
+// previous photon's bucket and its own (exclusive/inclusive), so every
+// bucket in [0, T] is written exactly once.
+__global__ void __launch_bounds__(256)
+k_cell_start(const uint32_t* __restrict__ keys, int64_t n, uint32_t T,
+             uint32_t* __restrict__ cell_start)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    const int64_t lo = (i == 0) ? 0 : (int64_t)keys[i - 1] + 1;
+    const int64_t hi = (i == n) ? (int64_t)T : (int64_t)keys[i];
+    for (int64_t c = lo; c <= hi; ++c) cell_start[c] = (uint32_t)i;
+}
+
+template <bool REC1, bool AUX>
+__global__ void __launch_bounds__(256)
+k_permute(int64_t n, const uint32_t* __restrict__ vals,
+          const float4* __restrict__ pack0, const float4* __restrict__ pack1,
+          const uint4* __restrict__ pack_aux, float4* __restrict__ rec0,
+          float4* __restrict__ rec1, uint4* __restrict__ aux)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t j = vals[i];
+    rec0[i] = pack0[j];
+    if (REC1) rec1[i] = pack1[j];
+    if (AUX) aux[i] = pack_aux[j];
+}
+
+template <int NCH, bool AUX, bool VCM>
+void launch_pack(ppm_ctx* c, const ppm_photons* ph, unsigned nb)
+{
+    k_pack_keys<NCH, AUX, VCM><<<nb, 256, 0, c->stream>>>(
+        ph->n, ph->pos, ph->flux, ph->nq, ph->rho, ph->wq, c->geom_dev,
+        c->sort.keys, c->sort.vals, c->pack0, c->pack1, c->pack_aux);
+}
+
+int reserve_photons(ppm_ctx* c, int64_t n)
+{
+    int rc = ppm_sort_scratch_reserve(&c->sort, n > 0 ? n : 1);
+    if (rc) return rc;
+    if (n <= c->ph_cap) return PPM_OK;
+    cudaFree(c->pack0); cudaFree(c->pack1); cudaFree(c->pack_aux);
+    cudaFree(c->rec0); cudaFree(c->rec1); cudaFree(c->aux);
+    c->pack0 = c->pack1 = c->rec0 = c->rec1 = nullptr;
+    c->pack_aux = c->aux = nullptr;
+    c->ph_cap = 0;
+    const int64_t cap = n + n / 4 + 1024;
+    const bool rec1 = c->nch == 3 || c->prm.vcm;
+    if (cudaMalloc(&c->pack0, cap * sizeof(float4)) != cudaSuccess ||
+        cudaMalloc(&c->rec0, cap * sizeof(float4)) != cudaSuccess ||
+        (rec1 && (cudaMalloc(&c->pack1, cap * sizeof(float4)) != cudaSuccess ||
+                  cudaMalloc(&c->rec1, cap * sizeof(float4)) != cudaSuccess)) ||
+        cudaMalloc(&c->pack_aux, cap * sizeof(uint4)) != cudaSuccess ||
+        cudaMalloc(&c->aux, cap * sizeof(uint4)) != cudaSuccess) {
+        cudaGetLastError();
+        return PPM_ENOMEM;
+    }
+    c->ph_cap = cap;
+    return PPM_OK;
+}
+
+}  // namespace
+
+// Bucket-table size: T = 2^tbits >= 2 n (so an empty cell lands on an
+// occupied bucket with probability <= 1/2 per photon-bucket), and at least
+// 4 blocks of B^3 cells.
+static int table_bits(int64_t n, int lb)
+{
+    int b = 3 * lb + 2;
+    while (b < 30 && ((int64_t)1 << b) < 2 * n) ++b;
+    return b;
+}
+
+int ppm_grid_build(ppm_ctx* c, const ppm_photons* ph)
+{
+    const int64_t n = ph->n;
+    int rc = reserve_photons(c, n);
+    if (rc) return rc;
+    const int lb = c->prm.cell_factor >= 1.0f ? 2 : 3;
+    c->tbits = table_bits(n, lb);
+    const uint32_t T = 1u << c->tbits;
+    if ((int64_t)T + 1 > c->cs_cap) {
+        cudaFree(c->cell_start);
+        c->cell_start = nullptr;
+        c->cs_cap = 0;
+        const int64_t cap = (int64_t)T + 1;
+        if (cudaMalloc(&c->cell_start, cap * sizeof(uint32_t)) != cudaSuccess) { cudaGetLastError(); return PPM_ENOMEM; }
+        c->cs_cap = cap;
+    }
+    c->lb = lb;
+    k_grid_geom<<<1, 1, 0, c->stream>>>(c->geom_dev, c->rmax + c->rmax_cur, c->prm.cell_factor, T - 1, lb);
+    PPM_LAUNCH_CHECK();
+    const bool aux = c->ph_aux;
+    const bool vcm = c->prm.vcm != 0;
+    if (n > 0) {
+        const unsigned nb = (unsigned)((n + 255) / 256);
+        if (c->nch == 3) {
+            if (vcm) launch_pack<3, true, true>(c, ph, nb);
+            else if (aux) launch_pack<3, true, false>(c, ph, nb);
+            else launch_pack<3, false, false>(c, ph, nb);
+        } else {
+            if (vcm) launch_pack<1, true, true>(c, ph, nb);
+            else if (aux) launch_pack<1, true, false>(c, ph, nb);
+            else launch_pack<1, false, false>(c, ph, nb);
+        }
+        PPM_LAUNCH_CHECK();
+        rc = ppm_radix_sort_pairs(&c->sort, n, c->tbits, c->stream);
+        if (rc) return rc;
+    }
+    k_cell_start<<<(unsigned)((n + 1 + 255) / 256), 256, 0, c->stream>>>(c->sort.keys, n, T, c->cell_start);
+    PPM_LAUNCH_CHECK();
+    if (n > 0) {
+        const unsigned nb = (unsigned)((n + 255) / 256);
+        const bool rec1 = c->nch == 3 || vcm;
+        if (rec1 && aux)
+            k_permute<true, true><<<nb, 256, 0, c->stream>>>(n, c->sort.vals, c->pack0, c->pack1, c->pack_aux, c->rec0, c->rec1, c->aux);
+        else if (rec1)
+            k_permute<true, false><<<nb, 256, 0, c->stream>>>(n, c->sort.vals, c->pack0, c->pack1, c->pack_aux, c->rec0, c->rec1, c->aux);
+        else if (aux)
+            k_permute<false, true><<<nb, 256, 0, c->stream>>>(n, c->sort.vals, c->pack0, c->pack1, c->pack_aux, c->rec0, c->rec1, c->aux);
+        else
+            k_permute<false, false><<<nb, 256, 0, c->stream>>>(n, c->sort.vals, c->pack0, c->pack1, c->pack_aux, c->rec0, c->rec1, c->aux);
+        PPM_LAUNCH_CHECK();
+    }
+    c->n_ph = n;
+    c->launches_build = 2 + (n > 0 ? 2 + 5 * ((c->tbits + 7) / 8) : 0);
+    return PPM_OK;
+}

@@ -1,0 +1,173 @@
+// ppm_internal.cuh -- shared declarations of the libppm CUDA sources.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ppm.h"
+
+#define PPM_NG 12
+
+// Return PPM_ECUDA from the enclosing function if a runtime call fails.
+#define PPM_CUDA(call)                                                       \
+    do {                                                                     \
+        cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess) { ppm_note_cuda_error(e_, #call, __FILE__, __LINE__); return PPM_ECUDA; } \
+    } while (0)
+
+#define PPM_LAUNCH_CHECK()                                                   \
+    do {                                                                     \
+        cudaError_t e_ = cudaGetLastError();                                 \
+        if (e_ != cudaSuccess) { ppm_note_cuda_error(e_, "launch", __FILE__, __LINE__); return PPM_ECUDA; } \
+    } while (0)
+
+void ppm_note_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+// ---------------------------------------------------------------------------
+// Grid: a uniform grid of cell edge h, hashed into T = 2^tbits buckets.
+// Cells are grouped in blocks of B^3 (B = 2^lb); the low 3*lb bits of a
+// bucket are the cell's coordinates inside its block, the high bits a hash
+// of the block coordinates.  Two consequences the gather relies on:
+//   * distinct cells less than B apart along every axis never share a
+//     bucket, so a hit point whose sphere spans <= B cells per axis visits
+//     each bucket at most once (no duplicate gathering);
+//   * cells consecutive along x inside one block have consecutive buckets,
+//     so a run of them is one contiguous range of the sorted photons.
+// ---------------------------------------------------------------------------
+struct GridGeom {
+    float inv_h;       // 1 / cell edge
+    float h;           // cell edge
+    uint32_t tmask;    // T - 1
+    int32_t lb;        // log2 of the block edge in cells (2 or 3)
+};
+
+__device__ __forceinline__ uint32_t ppm_fmix32(uint32_t x)
+{
+    // 32-bit finalizer of MurmurHash3 (Appleby): a bijective avalanche mix.
+    x ^= x >> 16; x *= 0x85ebca6bu;
+    x ^= x >> 13; x *= 0xc2b2ae35u;
+    x ^= x >> 16;
+    return x;
+}
+
+__device__ __forceinline__ int ppm_cell_coord(float p, float inv_h)
+{
+    float c = floorf(__fmul_rn(p, inv_h));
+    c = fminf(fmaxf(c, -1073741824.0f), 1073741824.0f);
+    return (int)c;
+}
+
+__device__ __forceinline__ uint32_t ppm_bucket(int ix, int iy, int iz, const GridGeom& g)
+{
+    const int lb = g.lb;
+    const uint32_t m = (1u << lb) - 1u;
+    uint32_t local = ((uint32_t)ix & m) | (((uint32_t)iy & m) << lb) | (((uint32_t)iz & m) << (2 * lb));
+    uint32_t bx = (uint32_t)(ix >> lb), by = (uint32_t)(iy >> lb), bz = (uint32_t)(iz >> lb);
+    uint32_t hb = ppm_fmix32(bx * 0x9E3779B1u ^ ppm_fmix32(by * 0x85EBCA77u ^ ppm_fmix32(bz + 0x27D4EB2Fu)));
+    return ((hb << (3 * lb)) | local) & g.tmask;
+}
+
+// Photon records in cell order.  rec0 = (x, y, z, psi) where psi is the
+// tested value of the photon before any VCM+ weight: the flux (1 channel)
+// or its luminance (3 channels).  rec1 = (R, G, B, rho_vm_l) for 3-channel
+// or VCM+ photons.  aux = (nq, wq, rho_vc_l bits, 0) when normals or VCM+.
+
+// ---------------------------------------------------------------------------
+// Device-wide primitives (ppm_sort.cu)
+// ---------------------------------------------------------------------------
+// Owner of the (key, value) arrays being sorted and of the sort's scratch:
+// both ping-pong pairs share one capacity, so swapping them is always safe.
+struct SortScratch {
+    uint32_t* keys = nullptr;
+    uint32_t* vals = nullptr;
+    uint32_t* keys_alt = nullptr;
+    uint32_t* vals_alt = nullptr;
+    uint32_t* hist = nullptr;       // 256 * ntiles
+    uint32_t* partials = nullptr;   // scan block partials
+    int64_t cap = 0;                // elements of each key/value array
+    int64_t hist_cap = 0;
+    int64_t part_cap = 0;
+};
+
+// Stable LSD radix sort of (s->keys, s->vals)[0, n) on the low `bits` bits
+// of the keys; the sorted pairs end up in (s->keys, s->vals) again (the
+// pointers are swapped with the alternates after each 8-bit pass).
+// Requires ppm_sort_scratch_reserve(s, >= n) first.
+int ppm_radix_sort_pairs(SortScratch* s, int64_t n, int bits, cudaStream_t st);
+int ppm_sort_scratch_reserve(SortScratch* s, int64_t n);
+void ppm_sort_scratch_free(SortScratch* s);
+
+// Exclusive prefix sum of n uint32 in place (partials: >= ceil(n/4096)+1).
+int ppm_exclusive_scan_u32(uint32_t* data, int64_t n, uint32_t* partials,
+                           cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// F critical values (ppm_fcrit.cu)
+// ---------------------------------------------------------------------------
+int ppm_fcrit_fill(double* table, int t_from, int t_to, double J, double alpha,
+                   cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+struct ppm_ctx {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    ppm_params prm{};
+    float r0 = 0.f, alpha = 0.75f, r_min = 0.f;
+    int64_t nh = 0;
+    int ntc = 1;          // tested channels
+    int nch = 1;          // flux channels
+    bool normals = false; // hit points carry normals
+    // hit points, spatially sorted
+    uint32_t* hp_orig = nullptr;  // sorted index -> caller index
+    float4* hp_pos = nullptr;     // x, y, z, nq bits
+    float4* hp_u = nullptr;       // ux, uy, uz, rho_vm_h
+    float4* hp_v = nullptr;       // vx, vy, vz, rho_vc_h
+    // state
+    float* r = nullptr;
+    int32_t* t = nullptr;
+    float* F = nullptr;
+    double* tau = nullptr;        // nh * nch
+    uint32_t* cnt = nullptr;      // [12][nh]
+    float* S = nullptr;           // [ntc][12][nh]
+    float* Q = nullptr;           // [ntc][12][nh]
+    // grid
+    int64_t ph_cap = 0;
+    int64_t n_ph = 0;             // photons in the current grid
+    int64_t J = 0;                // light paths per iteration (fixed)
+    int tbits = 0;
+    uint32_t* cell_start = nullptr;   // T + 1
+    int64_t cs_cap = 0;
+    float4* rec0 = nullptr;
+    float4* rec1 = nullptr;
+    uint4* aux = nullptr;
+    float4* pack0 = nullptr;      // unsorted packed records
+    float4* pack1 = nullptr;
+    uint4* pack_aux = nullptr;
+    SortScratch sort;
+    GridGeom* geom_dev = nullptr;     // written on the device by the build
+    int lb = 2;
+    bool grid_valid = false;
+    bool ph_aux = false;              // photon records carry the aux word
+    bool use_normals = false;         // same-surface filter this iteration
+    // radius bookkeeping: rmax[cur] is the max radius the current grid was
+    // built for; the update writes rmax[cur ^ 1]
+    float* rmax = nullptr;        // 2 floats
+    int rmax_cur = 0;
+    // F_c table, indexed by window length t' (1-based)
+    double* fc = nullptr;
+    int fc_cap = 0;
+    int fc_upto = 0;
+    // counters: [0] pairs, [1] candidates, [2] rejects, [3] pairs_total
+    unsigned long long* counters = nullptr;
+    int32_t* err_dev = nullptr;       // device error flags (bit 0: span > block)
+    int32_t iter = 0;
+    int32_t launches_build = 0;       // kernels launched by the last build
+    int32_t launches_iter = 0;        // ... by the last build + gather
+};
+
+// ppm_grid.cu / ppm_gather.cu
+int ppm_grid_build(ppm_ctx* c, const ppm_photons* ph);
+int ppm_gather_launch(ppm_ctx* c, float bound);
+int ppm_radiance_launch(ppm_ctx* c, float* out);

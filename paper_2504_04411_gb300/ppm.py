@@ -1,0 +1,253 @@
+"""Thin ctypes binding of libppm (include/ppm.h), same names as the C ABI.
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  Tensors are torch CUDA tensors; their device pointers and the
+current torch stream are passed straight through.  There is no CPU fallback:
+if libppm.so is missing or fails to load, the import of this module's
+functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libppm.so")
+
+PPM_OK, PPM_EINVAL, PPM_ENOMEM, PPM_ECUDA, PPM_ETIMEOUT, PPM_ESTATE = 0, -1, -2, -3, -4, -5
+PPM_NGROUPS = 12
+
+c_p = ctypes.c_void_p
+
+
+class ppm_hitpoints(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("pos", c_p), ("u", c_p), ("v", c_p),
+                ("nq", c_p), ("rho", c_p)]
+
+
+class ppm_photons(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("J", ctypes.c_int64), ("pos", c_p),
+                ("flux", c_p), ("channels", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("nq", c_p), ("rho", c_p), ("wq", c_p)]
+
+
+class ppm_params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_float), ("alpha_f", ctypes.c_float),
+                ("rmin_ratio", ctypes.c_float), ("cell_factor", ctypes.c_float),
+                ("channels", ctypes.c_int32), ("rgb_test", ctypes.c_int32),
+                ("vcm", ctypes.c_int32), ("n_vm", ctypes.c_float),
+                ("mapping", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class ppm_iter_stats(ctypes.Structure):
+    _fields_ = [("iter", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("pairs", ctypes.c_int64), ("candidates", ctypes.c_int64),
+                ("rejects", ctypes.c_int64), ("pairs_total", ctypes.c_int64),
+                ("r_max", ctypes.c_float), ("cell", ctypes.c_float),
+                ("launches", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class ppm_state_view(ctypes.Structure):
+    _fields_ = [("r", c_p), ("t", c_p), ("counts", c_p), ("S", c_p), ("Q", c_p),
+                ("tau", c_p), ("F", c_p)]
+
+
+# every symbol include/ppm.h declares
+EXPORTS = ("ppm_default_params", "ppm_create", "ppm_set_stream", "ppm_build_grid",
+           "ppm_gather_test_update", "ppm_radiance", "ppm_get_state", "ppm_set_state",
+           "ppm_set_iteration", "ppm_stats", "ppm_f_critical", "ppm_destroy",
+           "ppm_strerror")
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libppm.so (built by paper_2504_04411_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libppm.so not built ({path}); run paper_2504_04411_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    L.ppm_default_params.restype = None
+    L.ppm_default_params.argtypes = [ctypes.POINTER(ppm_params)]
+    L.ppm_create.restype = ctypes.c_int
+    L.ppm_create.argtypes = [ctypes.POINTER(ppm_hitpoints), ctypes.c_float, ctypes.c_float,
+                             ctypes.POINTER(ppm_params), c_p, ctypes.POINTER(c_p)]
+    L.ppm_set_stream.restype = ctypes.c_int
+    L.ppm_set_stream.argtypes = [c_p, c_p]
+    L.ppm_build_grid.restype = ctypes.c_int
+    L.ppm_build_grid.argtypes = [c_p, ctypes.POINTER(ppm_photons)]
+    L.ppm_gather_test_update.restype = ctypes.c_int
+    L.ppm_gather_test_update.argtypes = [c_p, ctypes.c_int32]
+    L.ppm_radiance.restype = ctypes.c_int
+    L.ppm_radiance.argtypes = [c_p, c_p]
+    L.ppm_get_state.restype = ctypes.c_int
+    L.ppm_get_state.argtypes = [c_p, ctypes.POINTER(ppm_state_view)]
+    L.ppm_set_state.restype = ctypes.c_int
+    L.ppm_set_state.argtypes = [c_p, ctypes.POINTER(ppm_state_view)]
+    L.ppm_set_iteration.restype = ctypes.c_int
+    L.ppm_set_iteration.argtypes = [c_p, ctypes.c_int32]
+    L.ppm_stats.restype = ctypes.c_int
+    L.ppm_stats.argtypes = [c_p, ctypes.POINTER(ppm_iter_stats)]
+    L.ppm_f_critical.restype = ctypes.c_int
+    L.ppm_f_critical.argtypes = [ctypes.c_int64, ctypes.c_float, ctypes.c_int32, c_p, c_p]
+    L.ppm_destroy.restype = None
+    L.ppm_destroy.argtypes = [c_p]
+    L.ppm_strerror.restype = ctypes.c_char_p
+    L.ppm_strerror.argtypes = [ctypes.c_int]
+    _lib = L
+    return L
+
+
+class PPMError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        msg = load().ppm_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{fn} returned {code} ({msg})")
+        self.code = code
+
+
+def _check(fn: str, rc: int) -> None:
+    if rc != PPM_OK:
+        raise PPMError(fn, rc)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libppm takes CUDA tensors")
+    if not t.is_contiguous():
+        raise ValueError("libppm takes contiguous tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------- C ABI ----
+def ppm_default_params() -> ppm_params:
+    p = ppm_params()
+    load().ppm_default_params(ctypes.byref(p))
+    return p
+
+
+def ppm_create(pos, u, v, r0: float, alpha: float = 0.75, params: ppm_params | None = None,
+               nq=None, rho=None, stream=None) -> ctypes.c_void_p:
+    """pos, u, v: (n,3) float32 CUDA tensors; nq (n,) int32/uint32 packed
+    normals or None; rho (n,2) float32 or None.  Returns the context handle."""
+    hp = ppm_hitpoints(pos.shape[0], _ptr(pos), _ptr(u), _ptr(v), _ptr(nq), _ptr(rho))
+    ctx = ctypes.c_void_p()
+    _check("ppm_create", load().ppm_create(ctypes.byref(hp), r0, alpha,
+                                           ctypes.byref(params) if params is not None else None,
+                                           _stream(stream), ctypes.byref(ctx)))
+    return ctx
+
+
+def ppm_set_stream(ctx, stream=None) -> None:
+    _check("ppm_set_stream", load().ppm_set_stream(ctx, _stream(stream)))
+
+
+def ppm_build_grid(ctx, pos, flux, J: int, nq=None, rho=None, wq=None) -> None:
+    channels = 3 if flux.dim() == 2 else 1
+    ph = ppm_photons(pos.shape[0], J, _ptr(pos), _ptr(flux), channels, 0,
+                     _ptr(nq), _ptr(rho), _ptr(wq))
+    _check("ppm_build_grid", load().ppm_build_grid(ctx, ctypes.byref(ph)))
+
+
+def ppm_gather_test_update(ctx, it: int) -> None:
+    _check("ppm_gather_test_update", load().ppm_gather_test_update(ctx, it))
+
+
+def ppm_radiance(ctx, out) -> None:
+    _check("ppm_radiance", load().ppm_radiance(ctx, _ptr(out)))
+
+
+def ppm_get_state(ctx, r=None, t=None, counts=None, S=None, Q=None, tau=None, F=None) -> None:
+    v = ppm_state_view(_ptr(r), _ptr(t), _ptr(counts), _ptr(S), _ptr(Q), _ptr(tau), _ptr(F))
+    _check("ppm_get_state", load().ppm_get_state(ctx, ctypes.byref(v)))
+
+
+def ppm_set_state(ctx, r=None, t=None, counts=None, S=None, Q=None, tau=None, F=None) -> None:
+    v = ppm_state_view(_ptr(r), _ptr(t), _ptr(counts), _ptr(S), _ptr(Q), _ptr(tau), _ptr(F))
+    _check("ppm_set_state", load().ppm_set_state(ctx, ctypes.byref(v)))
+
+
+def ppm_set_iteration(ctx, it: int) -> None:
+    _check("ppm_set_iteration", load().ppm_set_iteration(ctx, it))
+
+
+def ppm_stats(ctx) -> ppm_iter_stats:
+    s = ppm_iter_stats()
+    _check("ppm_stats", load().ppm_stats(ctx, ctypes.byref(s)))
+    return s
+
+
+def ppm_f_critical(J: int, alpha_f: float, t_max: int, out, stream=None) -> None:
+    _check("ppm_f_critical", load().ppm_f_critical(J, alpha_f, t_max, _ptr(out), _stream(stream)))
+
+
+def ppm_destroy(ctx) -> None:
+    if ctx:
+        load().ppm_destroy(ctx)
+
+
+def ppm_strerror(code: int) -> str:
+    return load().ppm_strerror(code).decode()
+
+
+# ----------------------------------------------------- convenience class ----
+class Estimator:
+    """Owns one context; `step(photons, it)` = build_grid + gather_test_update."""
+
+    def __init__(self, hp, r0: float, alpha: float = 0.75, params: ppm_params | None = None,
+                 stream=None):
+        self.n = int(hp.pos.shape[0])
+        self.params = params if params is not None else ppm_default_params()
+        self.channels = int(self.params.channels)
+        self.ntc = 3 if self.params.rgb_test else 1
+        self.ctx = ppm_create(hp.pos, hp.u, hp.v, r0, alpha, self.params,
+                              nq=hp.nq, rho=hp.rho if self.params.vcm else None, stream=stream)
+        self.it = 0
+
+    def step(self, ph, J: int | None = None) -> None:
+        ppm_build_grid(self.ctx, ph.pos, ph.flux, J if J is not None else ph.pos.shape[0],
+                       nq=ph.nq, rho=ph.rho if self.params.vcm else None,
+                       wq=ph.wq if self.params.vcm else None)
+        self.it += 1
+        ppm_gather_test_update(self.ctx, self.it)
+
+    def radiance(self) -> torch.Tensor:
+        shape = (self.n,) if self.channels == 1 else (self.n, 3)
+        out = torch.empty(shape, device="cuda", dtype=torch.float32)
+        ppm_radiance(self.ctx, out)
+        return out
+
+    def state(self) -> dict:
+        n, d = self.n, "cuda"
+        st = {"r": torch.empty(n, device=d), "t": torch.empty(n, device=d, dtype=torch.int32),
+              "counts": torch.empty(n, PPM_NGROUPS, device=d, dtype=torch.int32),
+              "S": torch.empty(n, self.ntc, PPM_NGROUPS, device=d),
+              "Q": torch.empty(n, self.ntc, PPM_NGROUPS, device=d),
+              "tau": torch.empty(n, self.channels, device=d, dtype=torch.float64),
+              "F": torch.empty(n, device=d)}
+        ppm_get_state(self.ctx, **st)
+        return st
+
+    def stats(self) -> ppm_iter_stats:
+        return ppm_stats(self.ctx)
+
+    def close(self) -> None:
+        ppm_destroy(self.ctx)
+        self.ctx = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            if self.ctx:
+                self.close()
+        except Exception:
+            pass

@@ -59,6 +59,20 @@ def test_fcrit_matches_scipy(d1, d2):
     assert O.f_crit(d1, d2, ALPHA) == pytest.approx(stats.f.ppf(1 - ALPHA, d1, d2), rel=1e-9)
 
 
+@pytest.mark.parametrize("J", [2, 1000, 2_000_000, 16_000_000])
+def test_fcrit_matches_high_precision_at_huge_d2(J):
+    # 40-digit evaluation of the same quantile (mpmath, independent code):
+    # d2 = 12 (t J - 1) reaches 6e10, where lgamma cancels in FP64
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    for t in [1, 64, 300]:
+        d2 = 12 * (t * J - 1)
+        a, b = mp.mpf(11) / 2, mp.mpf(d2) / 2
+        ex = mp.findroot(lambda F: mp.betainc(a, b, 0, 11 * F / (11 * F + d2), regularized=True)
+                         - (1 - mp.mpf(ALPHA)), mp.mpf("2.5"))
+        assert O.f_crit(11, d2, ALPHA) == pytest.approx(float(ex), rel=2e-12)
+
+
 def test_betainc_matches_scipy():
     from scipy import special
     rng = np.random.default_rng(1)

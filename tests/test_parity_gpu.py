@@ -1,0 +1,280 @@
+"""CUDA path (through the C ABI) against the CPU oracle, element by element,
+on the same seeded photons.  Counts, groups, radii and reject decisions are
+compared exactly (decisions outside a 1e-3 band around F_c); window sums,
+F and the estimate within the stated tolerances (tests/parity.py)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2504_04411_gb300 import synth
+
+from parity import compare, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _params(**kw):
+    from paper_2504_04411_gb300 import ppm
+    p = ppm.ppm_default_params()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+# ------------------------------------------------------------------ F_c ----
+@pytest.mark.parametrize("J", [2, 10, 1000, 100_000, 2_000_000, 16_000_000])
+def test_fcrit_table_matches_oracle(J):
+    import torch
+    from paper_2504_04411_gb300 import ppm
+    tmax = 300
+    out = torch.empty(tmax + 1, device="cuda", dtype=torch.float64)
+    ppm.ppm_f_critical(J, 0.01, tmax, out)
+    got = out.cpu().numpy()
+    assert got[0] == 0.0
+    for t in [1, 2, 3, 7, 16, 64, 199, 256, 300]:
+        want = O.f_crit(11, 12 * (t * J - 1), 0.01)
+        assert got[t] == pytest.approx(want, rel=1e-11), (t, got[t], want)
+
+
+def test_fcrit_other_alpha_and_monotone():
+    import torch
+    from paper_2504_04411_gb300 import ppm
+    out = torch.empty(65, device="cuda", dtype=torch.float64)
+    for a in [0.05, 0.1]:
+        ppm.ppm_f_critical(5000, a, 64, out)
+        got = out.cpu().numpy()
+        assert np.all(np.diff(got[1:]) < 0)   # more samples: smaller F_c
+        for t in [1, 9, 64]:
+            assert got[t] == pytest.approx(O.f_crit(11, 12 * (t * 5000 - 1), a), rel=1e-11)
+
+
+# --------------------------------------------------------- plane scenes ----
+def test_tiny_config_full_trajectory():
+    """64x64 hit points on z=0, r0=0.02, 16 iterations of 100k photons with
+    a step edge at x=0.5: the whole trajectory against the oracle."""
+    sc = synth.PlaneScene(nside=64, J=100_000, r0=0.02, step=True)
+    iters = 16
+    hp = sc.hitpoints("cuda")
+    batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
+    states, stats, L = run_gpu(hp, batches, sc.r0)
+    ref = O.run(hp.numpy(), synth.stack_numpy(batches), sc.r0, iters)
+    rep = compare(states, stats, L, ref, iters)
+    assert rep.diverged <= 4, rep
+    assert rep.max_rel_F < 1e-3
+    # the method really shrinks at the edge
+    assert ref.reject.sum() > 50
+
+
+def test_ragged_count_and_small_radius():
+    """A hit-point count that is not a multiple of the block size, radii
+    smaller than the cell, hit points outside the photon square."""
+    sc = synth.PlaneScene(nside=37, J=30_000, r0=0.013, step=True, lo=0.1, hi=0.9,
+                          seed=synth.SEED_BASE + 7)
+    iters = 6
+    hp = sc.hitpoints("cuda")
+    batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
+    states, stats, L = run_gpu(hp, batches, sc.r0, params=_params(cell_factor=2.0))
+    ref = O.run(hp.numpy(), synth.stack_numpy(batches), sc.r0, iters)
+    compare(states, stats, L, ref, iters)
+
+
+@pytest.mark.parametrize("cf", [0.5, 1.0, 4.0])
+def test_cell_factor_does_not_change_results(cf):
+    sc = synth.PlaneScene(nside=20, J=20_000, r0=0.05, step=True, seed=synth.SEED_BASE + 8)
+    iters = 4
+    hp = sc.hitpoints("cuda")
+    batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
+    states, stats, L = run_gpu(hp, batches, sc.r0, params=_params(cell_factor=cf))
+    ref = O.run(hp.numpy(), synth.stack_numpy(batches), sc.r0, iters)
+    compare(states, stats, L, ref, iters)
+
+
+# ------------------------------------------------------------ box scenes ---
+def _box(nh=3001, J=30_000, rgb=False, vcm=False, seed=0):
+    return synth.BoxScene(nh=nh, J=J, r0=0.04, rgb=rgb, vcm=vcm, seed=synth.SEED_BASE + 20 + seed)
+
+
+def test_box_scene_normals_lobes_shadows():
+    sc = _box()
+    iters = 8
+    hp = sc.hitpoints("cuda")
+    batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
+    states, stats, L = run_gpu(hp, batches, sc.r0)
+    ref = O.run(hp.numpy(), synth.stack_numpy(batches), sc.r0, iters)
+    rep = compare(states, stats, L, ref, iters)
+    assert rep.diverged <= 3
+
+
+def test_box_scene_rgb_luminance_test():
+    sc = _box(rgb=True, seed=1)
+    iters = 5
+    hp = sc.hitpoints("cuda")
+    batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
+    states, stats, L = run_gpu(hp, batches, sc.r0, params=_params(channels=3))
+    ref = O.run(hp.numpy(), synth.stack_numpy(batches), sc.r0, iters)
+    compare(states, stats, L, ref, iters)
+
+
+def test_box_scene_rgb_per_channel_test():
+    sc = _box(rgb=True, seed=2)
+    iters = 5
+    hp = sc.hitpoints("cuda")
+    batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
+    states, stats, L = run_gpu(hp, batches, sc.r0, params=_params(channels=3, rgb_test=1))
+    ref = O.run(hp.numpy(), synth.stack_numpy(batches), sc.r0, iters, rgb_test=True)
+    compare(states, stats, L, ref, iters)
+
+
+@pytest.mark.parametrize("rgb", [False, True])
+def test_box_scene_vcm_merge_weights(rgb):
+    sc = _box(rgb=rgb, vcm=True, seed=3)
+    iters = 5
+    hp = sc.hitpoints("cuda")
+    batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
+    p = _params(channels=3 if rgb else 1, vcm=1, k=0.9)
+    states, stats, L = run_gpu(hp, batches, sc.r0, params=p)
+    ref = O.run(hp.numpy(), synth.stack_numpy(batches), sc.r0, iters, k=0.9, vcm=True)
+    compare(states, stats, L, ref, iters)
+
+
+# ------------------------------------------------------------ edge cases ---
+def test_empty_iterations_and_single_hit_point():
+    import torch
+    from paper_2504_04411_gb300 import ppm
+    sc = synth.PlaneScene(nside=1, J=5000, r0=0.3, step=False)
+    hp = sc.hitpoints("cuda")
+    est = ppm.Estimator(hp, sc.r0)
+    empty_pos = torch.empty(0, 3, device="cuda")
+    empty_flux = torch.empty(0, device="cuda")
+    ppm.ppm_build_grid(est.ctx, empty_pos, empty_flux, J=5000)
+    ppm.ppm_gather_test_update(est.ctx, 1)
+    st = est.state()
+    assert int(st["t"][0]) == 1 and float(st["r"][0]) == pytest.approx(0.3)
+    assert est.stats().pairs == 0
+    ph = sc.photons(2, "cuda")
+    est.step(ph)
+    s = est.stats()
+    assert s.pairs > 0 and s.iter == 2
+    L = est.radiance().cpu().numpy()
+    ref = O.run(hp.numpy(), synth.stack_numpy([ph]), sc.r0, 1)
+    assert L[0] == pytest.approx(ref.tau[0, 0] / 2, rel=1e-5)
+    est.close()
+
+
+def test_no_hit_points():
+    import torch
+    from paper_2504_04411_gb300 import ppm
+    z = torch.empty(0, 3, device="cuda")
+    ctx = ppm.ppm_create(z, z, z, 0.1)
+    ph = synth.PlaneScene(J=1000).photons(1, "cuda")
+    ppm.ppm_build_grid(ctx, ph.pos, ph.flux, J=1000)
+    ppm.ppm_gather_test_update(ctx, 1)
+    ppm.ppm_radiance(ctx, torch.empty(0, device="cuda"))
+    assert ppm.ppm_stats(ctx).pairs == 0
+    ppm.ppm_destroy(ctx)
+
+
+def test_argument_and_sequence_errors():
+    import torch
+    from paper_2504_04411_gb300 import ppm
+    sc = synth.PlaneScene(nside=4, J=1000)
+    hp = sc.hitpoints("cuda")
+    with pytest.raises(ppm.PPMError) as e:
+        ppm.ppm_create(hp.pos, hp.u, hp.v, -1.0)
+    assert e.value.code == ppm.PPM_EINVAL
+    with pytest.raises(ppm.PPMError):
+        ppm.ppm_create(hp.pos, hp.u, hp.v, 0.1, alpha=1.5)
+    with pytest.raises(ppm.PPMError):
+        ppm.ppm_create(hp.pos, hp.u, hp.v, 0.1, params=_params(cell_factor=0.1))
+    with pytest.raises(ppm.PPMError):
+        ppm.ppm_create(hp.pos, hp.u, hp.v, 0.1, params=_params(vcm=1))   # no rho / normals
+    est = ppm.Estimator(hp, 0.1)
+    with pytest.raises(ppm.PPMError) as e:
+        ppm.ppm_gather_test_update(est.ctx, 1)          # no grid yet
+    assert e.value.code == ppm.PPM_ESTATE
+    ph = sc.photons(1, "cuda")
+    with pytest.raises(ppm.PPMError) as e:
+        ppm.ppm_build_grid(est.ctx, ph.pos, ph.flux, J=1)   # J < 2
+    assert e.value.code == ppm.PPM_EINVAL
+    with pytest.raises(ppm.PPMError):
+        ppm.ppm_build_grid(est.ctx, ph.pos, torch.zeros(1000, 3, device="cuda"), J=1000)  # channels
+    ppm.ppm_build_grid(est.ctx, ph.pos, ph.flux, J=1000)
+    with pytest.raises(ppm.PPMError) as e:
+        ppm.ppm_gather_test_update(est.ctx, 2)          # skipped iteration 1
+    assert e.value.code == ppm.PPM_ESTATE
+    ppm.ppm_gather_test_update(est.ctx, 1)
+    with pytest.raises(ppm.PPMError):
+        ppm.ppm_build_grid(est.ctx, ph.pos, ph.flux, J=999)  # J changed
+    est.close()
+
+
+def test_deterministic_and_resumable():
+    """Two runs give bitwise-identical state; a context resumed from a
+    checkpoint continues exactly like the straight run."""
+    import torch
+    from paper_2504_04411_gb300 import ppm
+    sc = _box(nh=2000, J=20000, seed=5)
+    hp = sc.hitpoints("cuda")
+    batches = [sc.photons(i, "cuda") for i in range(1, 7)]
+    runs = []
+    for _ in range(2):
+        est = ppm.Estimator(hp, sc.r0)
+        for ph in batches:
+            est.step(ph)
+        runs.append({k: v.cpu() for k, v in est.state().items()})
+        est.close()
+    for k in runs[0]:
+        assert torch.equal(runs[0][k], runs[1][k]), k
+    est = ppm.Estimator(hp, sc.r0)
+    for ph in batches[:3]:
+        est.step(ph)
+    ck = est.state()
+    est.close()
+    est2 = ppm.Estimator(hp, sc.r0)
+    ppm.ppm_set_state(est2.ctx, **ck)
+    ppm.ppm_set_iteration(est2.ctx, 3)
+    est2.it = 3
+    for ph in batches[3:]:
+        est2.step(ph)
+    fin = {k: v.cpu() for k, v in est2.state().items()}
+    est2.close()
+    for k in fin:
+        assert torch.equal(fin[k], runs[0][k]), k
+
+
+# -------------------------------------------- full size, sampled outputs ---
+def test_frame_config_full_size_sampled():
+    """1920x1080 hit points on three faces, 2M photons per iteration, the
+    launch configuration the benchmark times; 2 iterations; 3000 random hit
+    points checked against the oracle."""
+    import torch
+    sc = synth.BoxScene()
+    hp = sc.hitpoints("cuda")
+    iters = 2
+    batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
+    from paper_2504_04411_gb300 import ppm
+    est = ppm.Estimator(hp, sc.r0)
+    sts = []
+    for ph in batches:
+        est.step(ph)
+        sts.append({k: v.cpu().numpy() for k, v in est.state().items()})
+        assert est.stats().flags == 0
+    L = est.radiance().cpu().numpy()
+    est.close()
+    rng = np.random.default_rng(11)
+    idx = np.sort(rng.choice(hp.n, 3000, replace=False))
+    sub = {k: v[idx] for k, v in hp.numpy().items()}
+    ref = O.run(sub, synth.stack_numpy(batches), sc.r0, iters)
+    sub_states = [{k: v[idx] for k, v in s.items()} for s in sts]
+    rep = compare(sub_states, [{"pairs": 0, "flags": 0}] * iters, L[idx], ref, iters,
+                  check_pairs=False)
+    assert rep.diverged <= 3
+    torch.cuda.synchronize()
