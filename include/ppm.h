@@ -91,8 +91,8 @@ typedef struct {
 
 /* Method parameters.  ppm_default_params() fills the paper's defaults. */
 typedef struct {
+    double alpha_f;     /* significance level alpha_F, 0.01 (Sec. 6.1.1) */
     float k;            /* shrinking ratio of Eq. (radiusupdate), 0.7 (Sec. 6.1.1) */
-    float alpha_f;      /* significance level alpha_F, 0.01 (Sec. 6.1.1) */
     float rmin_ratio;   /* r_min = rmin_ratio * r0, 0.001 (Sec. 6.1.2) */
     float cell_factor;  /* grid cell edge = cell_factor * max radius, in [0.5, 4]; 1 */
     int32_t channels;   /* flux channels of every iteration: 1 or 3 */
@@ -101,7 +101,7 @@ typedef struct {
     int32_t vcm;        /* 1: weight samples by the VCM+ merge weight */
     float n_vm;         /* VCM+: light sub-paths used for merging; 0 = J */
     int32_t mapping;    /* gather mapping: 0 = default (thread per hit point) */
-    int32_t reserved[7];
+    int32_t reserved[6];
 } ppm_params;
 
 /* Per-iteration counters of the last ppm_gather_test_update. */
@@ -182,7 +182,7 @@ int ppm_stats(ppm_ctx* ctx, ppm_iter_stats* out);
 /* F-test critical values on their own (Sec. 3.2.2): out[t] = the
  * (1 - alpha_f) quantile of F(11, 12 (t J - 1)) for t = 1 .. t_max, FP64,
  * out[0] = 0.  out: device array of t_max + 1 doubles.  Enqueued on stream. */
-int ppm_f_critical(int64_t J, float alpha_f, int32_t t_max, double* out, void* stream);
+int ppm_f_critical(int64_t J, double alpha_f, int32_t t_max, double* out, void* stream);
 
 /* Frees everything the context owns (waits for the stream first). */
 void ppm_destroy(ppm_ctx* ctx);

@@ -161,7 +161,7 @@ int ensure_fc(ppm_ctx* c, int upto, int* launches)
     }
     // fill up to the capacity in one launch: later iterations hit the table
     const int to = c->fc_cap;
-    int rc = ppm_fcrit_fill(c->fc, c->fc_upto + 1, to, (double)c->J, (double)c->prm.alpha_f, c->stream);
+    int rc = ppm_fcrit_fill(c->fc, c->fc_upto + 1, to, (double)c->J, c->prm.alpha_f, c->stream);
     if (rc) return rc;
     c->fc_upto = to;
     return PPM_OK;
@@ -191,7 +191,7 @@ void ppm_default_params(ppm_params* p)
     if (!p) return;
     memset(p, 0, sizeof(*p));
     p->k = 0.7f;
-    p->alpha_f = 0.01f;
+    p->alpha_f = 0.01;
     p->rmin_ratio = 0.001f;
     p->cell_factor = 1.0f;
     p->channels = 1;
@@ -224,7 +224,7 @@ int ppm_create(const ppm_hitpoints* hp, float r0, float alpha, const ppm_params*
     if (!finite_pos(r0) || !(alpha > 0.f && alpha < 1.f)) return PPM_EINVAL;
     ppm_params prm;
     if (params) prm = *params; else ppm_default_params(&prm);
-    if (!(prm.k > 0.f && prm.k < 1.f) || !(prm.alpha_f > 0.f && prm.alpha_f < 1.f)) return PPM_EINVAL;
+    if (!(prm.k > 0.f && prm.k < 1.f) || !(prm.alpha_f > 0.0 && prm.alpha_f < 1.0)) return PPM_EINVAL;
     if (!(prm.rmin_ratio >= 0.f && prm.rmin_ratio < 1.f)) return PPM_EINVAL;
     if (!(prm.cell_factor >= 0.5f && prm.cell_factor <= 4.0f)) return PPM_EINVAL;
     if (prm.channels != 1 && prm.channels != 3) return PPM_EINVAL;
@@ -414,12 +414,12 @@ int ppm_stats(ppm_ctx* c, ppm_iter_stats* out)
     return PPM_OK;
 }
 
-int ppm_f_critical(int64_t J, float alpha_f, int32_t t_max, double* out, void* stream)
+int ppm_f_critical(int64_t J, double alpha_f, int32_t t_max, double* out, void* stream)
 {
-    if (J < 2 || !(alpha_f > 0.f && alpha_f < 1.f) || t_max < 1 || !out) return PPM_EINVAL;
+    if (J < 2 || !(alpha_f > 0.0 && alpha_f < 1.0) || t_max < 1 || !out) return PPM_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     PPM_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
-    return ppm_fcrit_fill(out, 1, t_max, (double)J, (double)alpha_f, st);
+    return ppm_fcrit_fill(out, 1, t_max, (double)J, alpha_f, st);
 }
 
 void ppm_destroy(ppm_ctx* c)

@@ -15,15 +15,16 @@
 // converges in a few dozen terms.  The quantile is found by Newton's
 // method on the CDF (derivative = the F density) kept inside a bisection
 // bracket.  d2 reaches ~1e11, where lgamma(b) - lgamma(a+b) loses ~1e-6 to
-// cancellation in FP64, so for large b that difference is taken from the
-// Stirling series of log Gamma written as a difference (no cancellation).
+// cancellation in FP64, so for b >= 64 that difference is taken from the
+// Stirling series of log Gamma written as a difference (no cancellation;
+// the first omitted term, 1/(1680 b^7), is below 1e-15 there).
 #include "ppm_internal.cuh"
 
 namespace {
 
 __device__ double lbeta_fp64(double a, double b)
 {
-    if (b < 1.0e4) return lgamma(a) + lgamma(b) - lgamma(a + b);
+    if (b < 64.0) return lgamma(a) + lgamma(b) - lgamma(a + b);
     // log G(b) - log G(a+b) from log G(z) = (z-1/2) log z - z + log(2 pi)/2
     //   + 1/(12 z) - 1/(360 z^3) + 1/(1260 z^5) - ...
     const double ab = a + b;

@@ -34,11 +34,11 @@ class ppm_photons(ctypes.Structure):
 
 
 class ppm_params(ctypes.Structure):
-    _fields_ = [("k", ctypes.c_float), ("alpha_f", ctypes.c_float),
+    _fields_ = [("alpha_f", ctypes.c_double), ("k", ctypes.c_float),
                 ("rmin_ratio", ctypes.c_float), ("cell_factor", ctypes.c_float),
                 ("channels", ctypes.c_int32), ("rgb_test", ctypes.c_int32),
                 ("vcm", ctypes.c_int32), ("n_vm", ctypes.c_float),
-                ("mapping", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("mapping", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class ppm_iter_stats(ctypes.Structure):
@@ -93,7 +93,7 @@ def load(path: str = LIB_PATH):
     L.ppm_stats.restype = ctypes.c_int
     L.ppm_stats.argtypes = [c_p, ctypes.POINTER(ppm_iter_stats)]
     L.ppm_f_critical.restype = ctypes.c_int
-    L.ppm_f_critical.argtypes = [ctypes.c_int64, ctypes.c_float, ctypes.c_int32, c_p, c_p]
+    L.ppm_f_critical.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_int32, c_p, c_p]
     L.ppm_destroy.restype = None
     L.ppm_destroy.argtypes = [c_p]
     L.ppm_strerror.restype = ctypes.c_char_p

@@ -156,6 +156,7 @@ def test_empty_iterations_and_single_hit_point():
     empty_flux = torch.empty(0, device="cuda")
     ppm.ppm_build_grid(est.ctx, empty_pos, empty_flux, J=5000)
     ppm.ppm_gather_test_update(est.ctx, 1)
+    est.it = 1
     st = est.state()
     assert int(st["t"][0]) == 1 and float(st["r"][0]) == pytest.approx(0.3)
     assert est.stats().pairs == 0
