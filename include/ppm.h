@@ -100,7 +100,9 @@ typedef struct {
                            RGB channel, reject if any rejects (Sec. 5.1) */
     int32_t vcm;        /* 1: weight samples by the VCM+ merge weight */
     float n_vm;         /* VCM+: light sub-paths used for merging; 0 = J */
-    int32_t mapping;    /* gather mapping: 0 = default (thread per hit point) */
+    int32_t mapping;    /* gather traversal: 0 = each thread walks its own cells,
+                           1 / 2 = warp walks the union of its 32 hit points'
+                           cells (32 / 64-entry in-disk queues per lane) */
     int32_t reserved[6];
 } ppm_params;
 

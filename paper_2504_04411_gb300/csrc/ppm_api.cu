@@ -50,6 +50,38 @@ __device__ __forceinline__ uint32_t spread3(uint32_t x)
     return x;
 }
 
+// Index of a point on the 3D Hilbert curve of order 10, from the
+// "transpose" formulation of J. Skilling, "Programming the Hilbert curve"
+// (AIP Conf. Proc. 707, 2004): undo the curve's excess rotations level by
+// level, Gray-encode, then interleave the bits (X[0] most significant).
+// Unlike Morton order the curve has no jumps, so any 32 consecutive hit
+// points form one compact patch -- the unit a warp gathers over.
+__device__ __forceinline__ uint32_t hilbert3(uint32_t x0, uint32_t x1, uint32_t x2)
+{
+    uint32_t X[3] = {x0, x1, x2};
+    const uint32_t M = 1u << 9;
+    for (uint32_t Q = M; Q > 1u; Q >>= 1) {
+        const uint32_t P = Q - 1u;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if (X[i] & Q) {
+                X[0] ^= P;
+            } else {
+                const uint32_t t = (X[0] ^ X[i]) & P;
+                X[0] ^= t;
+                X[i] ^= t;
+            }
+        }
+    }
+    X[1] ^= X[0];
+    X[2] ^= X[1];
+    uint32_t t = 0;
+    for (uint32_t Q = M; Q > 1u; Q >>= 1)
+        if (X[2] & Q) t ^= Q - 1u;
+    X[0] ^= t; X[1] ^= t; X[2] ^= t;
+    return (spread3(X[0]) << 2) | (spread3(X[1]) << 1) | spread3(X[2]);
+}
+
 __global__ void k_morton(int64_t n, const float* __restrict__ pos, const uint32_t* __restrict__ bb,
                          uint32_t* __restrict__ keys, uint32_t* __restrict__ vals)
 {
@@ -64,7 +96,7 @@ __global__ void k_morton(int64_t n, const float* __restrict__ pos, const uint32_
         f = fminf(fmaxf(f, 0.f), 1.f);
         q[d] = (uint32_t)(f * 1023.0f);
     }
-    keys[i] = spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
+    keys[i] = hilbert3(q[0], q[1], q[2]);
     vals[i] = (uint32_t)i;
 }
 
@@ -231,6 +263,7 @@ int ppm_create(const ppm_hitpoints* hp, float r0, float alpha, const ppm_params*
     if (prm.rgb_test && prm.channels != 3) return PPM_EINVAL;
     if (prm.vcm && hp->n > 0 && (!hp->rho || !hp->nq)) return PPM_EINVAL;
     if (prm.n_vm < 0.f) return PPM_EINVAL;
+    if (prm.mapping < 0 || prm.mapping > 2) return PPM_EINVAL;
 
     ppm_ctx* c = new (std::nothrow) ppm_ctx();
     if (!c) return PPM_ENOMEM;
@@ -256,7 +289,7 @@ int ppm_create(const ppm_hitpoints* hp, float r0, float alpha, const ppm_params*
     int rc = PPM_OK;
     do {
         if (n > 0) {
-            // spatial order: 30-bit Morton code of the position in the
+            // spatial order: 30-bit Hilbert index of the position in the
             // hit points' bounding box, stable radix sort
             SortScratch hs;
             uint32_t* bb = nullptr;

@@ -57,14 +57,18 @@ def test_fcrit_other_alpha_and_monotone():
 
 
 # --------------------------------------------------------- plane scenes ----
-def test_tiny_config_full_trajectory():
+MAPPINGS = [0, 1, 2]
+
+
+@pytest.mark.parametrize("mapping", MAPPINGS)
+def test_tiny_config_full_trajectory(mapping):
     """64x64 hit points on z=0, r0=0.02, 16 iterations of 100k photons with
     a step edge at x=0.5: the whole trajectory against the oracle."""
     sc = synth.PlaneScene(nside=64, J=100_000, r0=0.02, step=True)
     iters = 16
     hp = sc.hitpoints("cuda")
     batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
-    states, stats, L = run_gpu(hp, batches, sc.r0)
+    states, stats, L = run_gpu(hp, batches, sc.r0, params=_params(mapping=mapping))
     ref = O.run(hp.numpy(), synth.stack_numpy(batches), sc.r0, iters)
     rep = compare(states, stats, L, ref, iters)
     assert rep.diverged <= 4, rep
@@ -86,13 +90,14 @@ def test_ragged_count_and_small_radius():
     compare(states, stats, L, ref, iters)
 
 
+@pytest.mark.parametrize("mapping", MAPPINGS)
 @pytest.mark.parametrize("cf", [0.5, 1.0, 4.0])
-def test_cell_factor_does_not_change_results(cf):
+def test_cell_factor_does_not_change_results(cf, mapping):
     sc = synth.PlaneScene(nside=20, J=20_000, r0=0.05, step=True, seed=synth.SEED_BASE + 8)
     iters = 4
     hp = sc.hitpoints("cuda")
     batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
-    states, stats, L = run_gpu(hp, batches, sc.r0, params=_params(cell_factor=cf))
+    states, stats, L = run_gpu(hp, batches, sc.r0, params=_params(cell_factor=cf, mapping=mapping))
     ref = O.run(hp.numpy(), synth.stack_numpy(batches), sc.r0, iters)
     compare(states, stats, L, ref, iters)
 
@@ -102,12 +107,13 @@ def _box(nh=3001, J=30_000, rgb=False, vcm=False, seed=0):
     return synth.BoxScene(nh=nh, J=J, r0=0.04, rgb=rgb, vcm=vcm, seed=synth.SEED_BASE + 20 + seed)
 
 
-def test_box_scene_normals_lobes_shadows():
+@pytest.mark.parametrize("mapping", MAPPINGS)
+def test_box_scene_normals_lobes_shadows(mapping):
     sc = _box()
     iters = 8
     hp = sc.hitpoints("cuda")
     batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
-    states, stats, L = run_gpu(hp, batches, sc.r0)
+    states, stats, L = run_gpu(hp, batches, sc.r0, params=_params(mapping=mapping))
     ref = O.run(hp.numpy(), synth.stack_numpy(batches), sc.r0, iters)
     rep = compare(states, stats, L, ref, iters)
     assert rep.diverged <= 3
@@ -133,13 +139,14 @@ def test_box_scene_rgb_per_channel_test():
     compare(states, stats, L, ref, iters)
 
 
+@pytest.mark.parametrize("mapping", MAPPINGS)
 @pytest.mark.parametrize("rgb", [False, True])
-def test_box_scene_vcm_merge_weights(rgb):
+def test_box_scene_vcm_merge_weights(rgb, mapping):
     sc = _box(rgb=rgb, vcm=True, seed=3)
     iters = 5
     hp = sc.hitpoints("cuda")
     batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
-    p = _params(channels=3 if rgb else 1, vcm=1, k=0.9)
+    p = _params(channels=3 if rgb else 1, vcm=1, k=0.9, mapping=mapping)
     states, stats, L = run_gpu(hp, batches, sc.r0, params=p)
     ref = O.run(hp.numpy(), synth.stack_numpy(batches), sc.r0, iters, k=0.9, vcm=True)
     compare(states, stats, L, ref, iters)
@@ -252,7 +259,8 @@ def test_deterministic_and_resumable():
 
 
 # -------------------------------------------- full size, sampled outputs ---
-def test_frame_config_full_size_sampled():
+@pytest.mark.parametrize("mapping", MAPPINGS)
+def test_frame_config_full_size_sampled(mapping):
     """1920x1080 hit points on three faces, 2M photons per iteration, the
     launch configuration the benchmark times; 2 iterations; 3000 random hit
     points checked against the oracle."""
@@ -262,7 +270,7 @@ def test_frame_config_full_size_sampled():
     iters = 2
     batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
     from paper_2504_04411_gb300 import ppm
-    est = ppm.Estimator(hp, sc.r0)
+    est = ppm.Estimator(hp, sc.r0, params=_params(mapping=mapping))
     sts = []
     for ph in batches:
         est.step(ph)
