@@ -186,6 +186,18 @@ int ppm_stats(ppm_ctx* ctx, ppm_iter_stats* out);
  * out[0] = 0.  out: device array of t_max + 1 doubles.  Enqueued on stream. */
 int ppm_f_critical(int64_t J, double alpha_f, int32_t t_max, double* out, void* stream);
 
+/* Stable LSD radix sort of (key, value) pairs on the low `bits` bits of the
+ * keys (1..32), the sort that orders photons by grid bucket in
+ * ppm_build_grid: pairs with equal keys keep their input order.  keys_in,
+ * vals_in: n uint32 each (device, read only); keys_out, vals_out: n uint32
+ * each (device, written; may alias the inputs).  n in [0, 2^32 - 1).
+ * Scratch (2n + 256 ceil(n/2048) words) comes from cudaMallocAsync on the
+ * stream and is released with cudaFreeAsync, so the call does not block.
+ * PPM_EINVAL for bad sizes or NULL pointers with n > 0, PPM_ENOMEM if the
+ * scratch cannot be allocated. */
+int ppm_sort_pairs(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                   uint32_t* vals_out, int64_t n, int32_t bits, void* stream);
+
 /* Frees everything the context owns (waits for the stream first). */
 void ppm_destroy(ppm_ctx* ctx);
 

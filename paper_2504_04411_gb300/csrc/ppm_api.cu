@@ -455,6 +455,47 @@ int ppm_f_critical(int64_t J, double alpha_f, int32_t t_max, double* out, void* 
     return ppm_fcrit_fill(out, 1, t_max, (double)J, alpha_f, st);
 }
 
+int ppm_sort_pairs(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                   uint32_t* vals_out, int64_t n, int32_t bits, void* stream)
+{
+    if (n < 0 || n >= 0xffffffffll || bits < 1 || bits > 32) return PPM_EINVAL;
+    if (n > 0 && (!keys_in || !vals_in || !keys_out || !vals_out)) return PPM_EINVAL;
+    if (n == 0) return PPM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (keys_out != keys_in)
+        PPM_CUDA(cudaMemcpyAsync(keys_out, keys_in, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+    if (vals_out != vals_in)
+        PPM_CUDA(cudaMemcpyAsync(vals_out, vals_in, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+    if (n == 1) return PPM_OK;
+    const int64_t ntiles = (n + 2047) / 2048;
+    const int64_t hist = 256 * ntiles;
+    const int64_t part = hist / 4096 + 2;
+    uint32_t* scratch = nullptr;
+    const size_t words = (size_t)(2 * n + hist + part);
+    if (cudaMallocAsync((void**)&scratch, words * sizeof(uint32_t), st) != cudaSuccess) {
+        cudaGetLastError();
+        return PPM_ENOMEM;
+    }
+    SortScratch s;
+    s.keys = keys_out;
+    s.vals = vals_out;
+    s.keys_alt = scratch;
+    s.vals_alt = scratch + n;
+    s.hist = scratch + 2 * n;
+    s.partials = scratch + 2 * n + hist;
+    s.cap = n;
+    s.hist_cap = hist;
+    s.part_cap = part;
+    int rc = ppm_radix_sort_pairs(&s, n, bits, st);
+    if (rc == PPM_OK && s.keys != keys_out) {   // odd number of passes
+        if (cudaMemcpyAsync(keys_out, s.keys, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(vals_out, s.vals, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            rc = PPM_ECUDA;
+    }
+    if (cudaFreeAsync(scratch, st) != cudaSuccess && rc == PPM_OK) rc = PPM_ECUDA;
+    return rc;
+}
+
 void ppm_destroy(ppm_ctx* c)
 {
     if (!c) return;

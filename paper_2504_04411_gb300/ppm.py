@@ -57,8 +57,8 @@ class ppm_state_view(ctypes.Structure):
 # every symbol include/ppm.h declares
 EXPORTS = ("ppm_default_params", "ppm_create", "ppm_set_stream", "ppm_build_grid",
            "ppm_gather_test_update", "ppm_radiance", "ppm_get_state", "ppm_set_state",
-           "ppm_set_iteration", "ppm_stats", "ppm_f_critical", "ppm_destroy",
-           "ppm_strerror")
+           "ppm_set_iteration", "ppm_stats", "ppm_f_critical", "ppm_sort_pairs",
+           "ppm_destroy", "ppm_strerror")
 
 _lib = None
 
@@ -94,6 +94,8 @@ def load(path: str = LIB_PATH):
     L.ppm_stats.argtypes = [c_p, ctypes.POINTER(ppm_iter_stats)]
     L.ppm_f_critical.restype = ctypes.c_int
     L.ppm_f_critical.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_int32, c_p, c_p]
+    L.ppm_sort_pairs.restype = ctypes.c_int
+    L.ppm_sort_pairs.argtypes = [c_p, c_p, c_p, c_p, ctypes.c_int64, ctypes.c_int32, c_p]
     L.ppm_destroy.restype = None
     L.ppm_destroy.argtypes = [c_p]
     L.ppm_strerror.restype = ctypes.c_char_p
@@ -189,6 +191,14 @@ def ppm_stats(ctx) -> ppm_iter_stats:
 
 def ppm_f_critical(J: int, alpha_f: float, t_max: int, out, stream=None) -> None:
     _check("ppm_f_critical", load().ppm_f_critical(J, alpha_f, t_max, _ptr(out), _stream(stream)))
+
+
+def ppm_sort_pairs(keys_in, vals_in, keys_out, vals_out, bits: int, stream=None) -> None:
+    """Stable radix sort of uint32 (key, value) pairs (int32 tensors holding
+    the bit patterns) on the low ``bits`` bits."""
+    _check("ppm_sort_pairs", load().ppm_sort_pairs(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out),
+                                                   _ptr(vals_out), keys_in.numel(), bits,
+                                                   _stream(stream)))
 
 
 def ppm_destroy(ctx) -> None:
