@@ -203,6 +203,29 @@ void ppm_destroy(ppm_ctx* ctx);
 
 const char* ppm_strerror(int code);
 
+/* ---- no-allocation variant (the paper has no counterpart) ----------------
+ * ppm_sort_pairs_noalloc: the same stable radix sort as ppm_sort_pairs, with
+ * the same arguments, results and error codes, for callers that must not
+ * allocate device memory while they run -- work recorded into a CUDA graph
+ * (stream capture forbids cudaMalloc), real-time loops that cannot pay for
+ * an allocator call or its implicit synchronization, hosts whose device
+ * memory belongs to another allocator.  It calls no cudaMalloc, cudaFree or
+ * other allocating routine: its scratch is a fixed device array of the
+ * library, sized for PPM_NOALLOC_MAX_PAIRS pairs (~8.6 MB), which every GPU
+ * that loads the library holds until the process exits.
+ *   - n > PPM_NOALLOC_MAX_PAIRS returns PPM_EINVAL (use ppm_sort_pairs).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the array: calls whose work overlaps on the GPU
+ *     (several streams or host threads on one device) race on it; order
+ *     them on one stream.  It keeps the last call's contents; nothing in it
+ *     needs clearing between calls. */
+#define PPM_NOALLOC_MAX_PAIRS (1 << 20)
+int ppm_sort_pairs_noalloc(const uint32_t* keys_in, const uint32_t* vals_in,
+                           uint32_t* keys_out, uint32_t* vals_out, int64_t n,
+                           int32_t bits, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

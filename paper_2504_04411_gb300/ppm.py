@@ -58,7 +58,7 @@ class ppm_state_view(ctypes.Structure):
 EXPORTS = ("ppm_default_params", "ppm_create", "ppm_set_stream", "ppm_build_grid",
            "ppm_gather_test_update", "ppm_radiance", "ppm_get_state", "ppm_set_state",
            "ppm_set_iteration", "ppm_stats", "ppm_f_critical", "ppm_sort_pairs",
-           "ppm_destroy", "ppm_strerror")
+           "ppm_destroy", "ppm_strerror", "ppm_sort_pairs_noalloc")
 
 _lib = None
 
@@ -96,6 +96,8 @@ def load(path: str = LIB_PATH):
     L.ppm_f_critical.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_int32, c_p, c_p]
     L.ppm_sort_pairs.restype = ctypes.c_int
     L.ppm_sort_pairs.argtypes = [c_p, c_p, c_p, c_p, ctypes.c_int64, ctypes.c_int32, c_p]
+    L.ppm_sort_pairs_noalloc.restype = ctypes.c_int
+    L.ppm_sort_pairs_noalloc.argtypes = [c_p, c_p, c_p, c_p, ctypes.c_int64, ctypes.c_int32, c_p]
     L.ppm_destroy.restype = None
     L.ppm_destroy.argtypes = [c_p]
     L.ppm_strerror.restype = ctypes.c_char_p
@@ -199,6 +201,18 @@ def ppm_sort_pairs(keys_in, vals_in, keys_out, vals_out, bits: int, stream=None)
     _check("ppm_sort_pairs", load().ppm_sort_pairs(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out),
                                                    _ptr(vals_out), keys_in.numel(), bits,
                                                    _stream(stream)))
+
+
+PPM_NOALLOC_MAX_PAIRS = 1 << 20
+
+
+def ppm_sort_pairs_noalloc(keys_in, vals_in, keys_out, vals_out, bits: int, stream=None) -> None:
+    """ppm_sort_pairs without any device allocation: scratch lives in a
+    fixed device array of the library (at most PPM_NOALLOC_MAX_PAIRS pairs;
+    calls that overlap on the GPU race on it)."""
+    _check("ppm_sort_pairs_noalloc",
+           load().ppm_sort_pairs_noalloc(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out),
+                                         _ptr(vals_out), keys_in.numel(), bits, _stream(stream)))
 
 
 def ppm_destroy(ctx) -> None:
