@@ -2,12 +2,21 @@
 
 A step is one iteration of the method over one batch of photons: build the
 photon grid (cell key, stable radix sort, cell ranges, permute) and gather /
-F-test / update every hit point.  Default workload: the frame-sized plain
-configuration -- 1920x1080 hit points on the three faces z=0, y=0, x=0 of the
-unit box, 2,000,000 photons per iteration (uniform density + 2 anisotropic
-Gaussian caustic lobes + 2 step-edge shadows), r0 = 0.01, 64 iterations in
-total (warm-up + timed).  Metric: in-disk photon/hit-point pair tests per
-second (pairs gathered by the gather's disk test), whole job.
+F-test / update every hit point.
+
+Workloads (--config):
+  frame    (default) 1920x1080 hit points on the three faces z=0, y=0, x=0 of
+           the unit box, 2,000,000 photons per iteration (uniform density +
+           2 anisotropic Gaussian caustic lobes + 2 step-edge shadows),
+           r0 = 0.01, 64 iterations in total (warm-up + timed);
+  tiny     64x64 hit points on one plane, 100k photons per iteration;
+  batched  256 independent problems (hit points log-uniform 1k-256k, photons
+           log-uniform 10k-1M per iteration, 1-3 random unit squares each) in
+           one persistent launch per iteration, replayed as a CUDA graph;
+           compared with the same problems run as separate contexts.
+The gather traversal and cell factor are picked by the autotuner before the
+timed region.  Metric: in-disk photon/hit-point pair tests per second (pairs
+that pass the gather's disk test), whole job.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
 bounded sample of the same workload instead.
@@ -17,7 +26,6 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -31,11 +39,12 @@ sys.path.insert(0, ROOT)
 METRIC = "photon-hitpoint pair tests/sec"
 UNIT = "pairs/s"
 
-# algorithmic bytes of the gather kernel (k_gather_update), per unit
-GATHER_BYTES_PER_PHOTON = 16 + 4          # sorted record + aux word (normals), read once
+# algorithmic bytes of one gather launch (k_gather_update), per unit
+GATHER_BYTES_PER_PHOTON = 16 + 4          # sorted record + normal word, read once
 GATHER_BYTES_PER_HIT = 48 + 4 + 4 + 8 + 144 + (4 + 4 + 8 + 4 + 144)
-# static record read; r, t, tau, window (12 x count/S/Q) read; r, t, tau, F, window written
-# algorithmic FP32/INT ops of the canonical per-pair sequence
+# static record read; r, t, tau and the window (12 x count, S, Q) read;
+# r, t, tau, F and the window written
+# algorithmic FP32/INT operations of the canonical per-pair sequence
 OPS_PER_CANDIDATE = 7     # 3 sub, 1 mul + 2 fma (d^2), 1 compare
 OPS_PER_PAIR = 28         # normal dp4a+cmp 2, map 6, rho^2 2, ring 2, sector 9, group 1, accumulate 4, flux 2
 
@@ -51,23 +60,29 @@ def _src_hash(path):
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
 
 
+def _gather_sources_hash():
+    h = hashlib.sha256()
+    for f in ("ppm_gather.cu", "ppm_gather_impl.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2504_04411_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def _profile_traffic(config):
     """dram bytes per gather launch from the committed ncu summary, if it was
-    taken on the current kernel source; else None."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    taken on the current gather source; else None."""
     try:
-        d = json.load(open(p))
+        d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
     except Exception:
         return None
     ent = d.get(config)
-    if not ent:
-        return None
-    if ent.get("src_sha") != _src_hash(os.path.join(ROOT, "paper_2504_04411_gb300", "csrc", "ppm_gather.cu")):
+    if not ent or ent.get("src_sha") != _gather_sources_hash():
         return None
     return ent.get("dram_bytes_per_launch")
 
 
 class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
     def __init__(self, dev_index=0):
         self.dev = dev_index
         self.proc = None
@@ -116,7 +131,7 @@ class ClockSampler:
 # ----------------------------------------------------------------- oracle --
 def oracle_sample(scene, batches_np, hp_np, n_hits, seed=0):
     """Run the CPU oracle (as it stands) over one iteration for a random
-    subset of hit points; returns (pairs, seconds, threads)."""
+    subset of hit points; returns (pairs, seconds)."""
     import numpy as np
 
     from oracle import oracle as O
@@ -133,7 +148,7 @@ def cpu_baseline(scene, hp_np, ph_np, budget_s=12.0):
     threads = os.cpu_count() or 1
     os.environ.setdefault("OMP_NUM_THREADS", str(threads))
     probe = 128
-    pairs, dt = oracle_sample(scene, ph_np, hp_np, probe, seed=1)
+    _, dt = oracle_sample(scene, ph_np, hp_np, probe, seed=1)
     n = int(min(hp_np["pos"].shape[0], max(probe, probe * budget_s / max(dt, 1e-3))))
     pairs, dt = oracle_sample(scene, ph_np, hp_np, n, seed=2)
     return {"value": pairs / dt, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", threads)),
@@ -146,14 +161,19 @@ def cpu_baseline(scene, hp_np, ph_np, budget_s=12.0):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=61)
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="frame", choices=["frame", "tiny"])
+    ap.add_argument("--config", default="frame", choices=["frame", "tiny", "batched"])
+    ap.add_argument("--mapping", type=int, default=None, help="skip the autotuner: traversal")
+    ap.add_argument("--cell-factor", type=float, default=None, help="skip the autotuner: cell factor")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.steps is None:
+        a.steps = 16 if a.config == "batched" else 64 - a.warmup
+    return a
 
 
 def make_scene(config, rank):
@@ -168,6 +188,25 @@ def make_scene(config, rank):
                             "2M photons/iter (uniform + 2 Gaussian caustic lobes + 2 step-edge shadows), r0=0.01",
                 "hit_points": sc.nh, "photons_per_iter": sc.J, "r0": sc.r0}
     return sc, desc
+
+
+def roofline(g_ms, photons, hits, candidates, pairs, sm_count, kernel):
+    peaks = _peaks()
+    g_s = g_ms / 1e3
+    bytes_launch = photons * GATHER_BYTES_PER_PHOTON + hits * GATHER_BYTES_PER_HIT
+    hbm_achieved = bytes_launch / g_s / 1e9
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    ops_launch = candidates * OPS_PER_CANDIDATE + pairs * OPS_PER_PAIR
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = sm_count * 128 * sm_mhz * 1e6 / 1e12
+    alu_achieved = ops_launch / g_s / 1e12
+    hbm = {"bound": "hbm", "achieved": round(hbm_achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+           "frac": round(hbm_achieved / hbm_peak, 4), "algorithmic_bytes": bytes_launch, "kernel": kernel,
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"}
+    alu = {"bound": "alu", "achieved": round(alu_achieved, 3), "peak": round(alu_peak, 2), "unit": "Tops/s",
+           "frac": round(alu_achieved / alu_peak, 4), "algorithmic_ops": ops_launch, "kernel": kernel,
+           "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (recipe unit counts, max clock)"}
+    return (alu, hbm) if alu["frac"] >= hbm["frac"] else (hbm, alu)
 
 
 def main():
@@ -191,31 +230,61 @@ def main():
     if dist:
         tdist.barrier()
     __graft_entry__.build()
-    from paper_2504_04411_gb300 import ppm, synth
+    if args.config == "batched":
+        line = run_batched(args, rank, world, local, dist)
+    else:
+        line = run_single(args, rank, world, local, dist)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        tdist.destroy_process_group()
+    return 0
 
+
+def _reduce(dist, seconds, count):
+    if not dist:
+        return seconds, float(count)
+    import torch
+    import torch.distributed as tdist
+    tm = torch.tensor([seconds], device="cuda", dtype=torch.float64)
+    tdist.all_reduce(tm, op=tdist.ReduceOp.MAX)
+    ts = torch.tensor([float(count)], device="cuda", dtype=torch.float64)
+    tdist.all_reduce(ts, op=tdist.ReduceOp.SUM)
+    return float(tm), float(ts)
+
+
+def run_single(args, rank, world, local, dist):
+    import torch
+
+    from paper_2504_04411_gb300 import autotune, ppm, synth
     sc, desc = make_scene(args.config, rank)
     W, K = args.warmup, args.steps
     hp = sc.hitpoints("cuda")
     batches = [sc.photons(i, "cuda") for i in range(1, W + K + 1)]
     torch.cuda.synchronize()
+    # autotuner: traversal and cell factor (before the timed region)
+    if args.mapping is not None and args.cell_factor is not None:
+        tuned = {"mapping": args.mapping, "cell_factor": args.cell_factor, "key": "given"}
+    else:
+        tuned = autotune.tune(hp, batches[:3], sc.r0)
+    params = ppm.ppm_default_params()
+    params.mapping, params.cell_factor = tuned["mapping"], tuned["cell_factor"]
     flush = None if args.no_flush else torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     stream = torch.cuda.current_stream()
-    est = ppm.Estimator(hp, sc.r0, 0.75)
+    est = ppm.Estimator(hp, sc.r0, 0.75, params)
     for i in range(W):
         est.step(batches[i])
     torch.cuda.synchronize()
-    st0 = est.stats()
-    pairs0 = st0.pairs_total
+    pairs0 = est.stats().pairs_total
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    cand = 0
-    launches = 0
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
     if dist:
+        import torch.distributed as tdist
         tdist.barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
@@ -237,83 +306,44 @@ def main():
     clk = clocks.stop()
     st = est.stats()
     pairs = st.pairs_total - pairs0
-    launches = st.launches * K
     step_ms = [a.elapsed_time(c) for a, b, c in ev]
     gather_ms = [b.elapsed_time(c) for a, b, c in ev]
     build_ms = [a.elapsed_time(b) for a, b, c in ev]
-    total_s = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([total_s, float(pairs)], device="cuda", dtype=torch.float64)
-        tmax = t[:1].clone()
-        tdist.all_reduce(tmax, op=tdist.ReduceOp.MAX)
-        tsum = t[1:].clone()
-        tdist.all_reduce(tsum, op=tdist.ReduceOp.SUM)
-        total_s, all_pairs = float(tmax), float(tsum)
-    else:
-        all_pairs = float(pairs)
+    total_s, all_pairs = _reduce(dist, sum(step_ms) / 1e3, pairs)
     value = all_pairs / total_s
-
-    # ---- roofline of the dominant kernel (the gather) ----------------------
-    peaks = _peaks()
-    g_s = statistics.mean(gather_ms) / 1e3
-    bytes_launch = sc.J * GATHER_BYTES_PER_PHOTON + hp.n * GATHER_BYTES_PER_HIT
-    hbm_achieved = bytes_launch / g_s / 1e9
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    ops_launch = (st.candidates * OPS_PER_CANDIDATE + st.pairs * OPS_PER_PAIR)
-    sm_count = torch.cuda.get_device_properties(0).multi_processor_count
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = sm_count * 128 * sm_mhz * 1e6 / 1e12      # Tops/s (FP32 lanes x clock)
-    alu_achieved = ops_launch / g_s / 1e12
-    hbm = {"bound": "hbm", "achieved": round(hbm_achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-           "frac": round(hbm_achieved / hbm_peak, 4), "traffic": _profile_traffic(args.config),
-           "algorithmic_bytes": bytes_launch, "kernel": "k_gather_update",
-           "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"}
-    alu = {"bound": "alu", "achieved": round(alu_achieved, 3), "peak": round(alu_peak, 2), "unit": "Tops/s",
-           "frac": round(alu_achieved / alu_peak, 4), "traffic": hbm["traffic"],
-           "algorithmic_ops": ops_launch, "kernel": "k_gather_update",
-           "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz"}
-    roof, other = (alu, hbm) if alu["frac"] >= hbm["frac"] else (hbm, alu)
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    roof, other = roofline(statistics.mean(gather_ms), sc.J, hp.n, st.candidates, st.pairs, sm_count,
+                           "k_gather_update")
+    roof["traffic"] = other["traffic"] = _profile_traffic(args.config)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": 1e3 * total_s / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(desc, l2="flushed between steps (256 MB write, untimed)" if flush is not None else "not flushed",
-                           parallelism=f"replicas x{world}" if world > 1 else "single GPU",
-                           iterations_total=W + K),
+            "config": dict(desc, l2="flushed between steps (256 MB write, untimed)" if flush is not None
+                           else "not flushed", parallelism=f"independent replicas x{world}" if world > 1
+                           else "single GPU", iterations_total=W + K, mapping=tuned["mapping"],
+                           cell_factor=tuned["cell_factor"], autotune_key=tuned.get("key")),
             "iterations_per_sec": K / total_s,
-            "candidates_per_sec": st.candidates * K / total_s if False else None,
             "build_ms": statistics.mean(build_ms), "gather_ms": statistics.mean(gather_ms),
-            "wall_s": wall, "gpu_launches": launches,
-            "roofline": roof, "roofline_other": other, "clocks": clk}
-    line["candidates_last_iter"] = st.candidates
-    line["pairs_last_iter"] = st.pairs
-    line["rejects_last_iter"] = st.rejects
-
-    # ---- end to end through the public API with host buffers -------------
+            "wall_s": wall, "gpu_launches": st.launches * K,
+            "roofline": roof, "roofline_other": other, "clocks": clk,
+            "candidates_last_iter": st.candidates, "pairs_last_iter": st.pairs,
+            "rejects_last_iter": st.rejects}
     if not args.no_e2e:
-        e2e = run_e2e(est, batches, W, K, stream, sc)
-        if dist:
-            t = torch.tensor([e2e["seconds"], float(e2e["pairs"])], device="cuda", dtype=torch.float64)
-            tm = t[:1].clone(); tdist.all_reduce(tm, op=tdist.ReduceOp.MAX)
-            ts = t[1:].clone(); tdist.all_reduce(ts, op=tdist.ReduceOp.SUM)
-            e2e["seconds"], e2e["pairs"] = float(tm), float(ts)
-        line["e2e"] = {"value": e2e["pairs"] / e2e["seconds"], "unit": UNIT,
-                       "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]}
+        e2e = run_e2e(est, batches, W, K)
+        secs, cnt = _reduce(dist, e2e["seconds"], e2e["pairs"])
+        line["e2e"] = {"value": cnt / secs, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
+                       "d2h_bytes_per_step": e2e["d2h"]}
     est.close()
-
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         hp_np = hp.numpy()
         ph_np = synth.stack_numpy([batches[W]])
         del batches
         line["cpu_baseline"] = cpu_baseline(sc, hp_np, ph_np)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if dist:
-        tdist.destroy_process_group()
-    return 0
+    return line
 
 
-def run_e2e(est, batches, W, K, stream, sc):
+def run_e2e(est, batches, W, K):
     """The same iterations through the public API with host-resident inputs:
     each step copies its photons from pinned host memory, runs the
     iteration, and reads the iteration's counters back."""
@@ -325,7 +355,6 @@ def run_e2e(est, batches, W, K, stream, sc):
         ph = batches[W + i]
         host.append((ph.pos.cpu().pin_memory(), ph.flux.cpu().pin_memory(), ph.nq.cpu().pin_memory()))
     h2d = sum(t.numel() * t.element_size() for t in host[0])
-    # continue the same estimator: the sequence stays valid
     torch.cuda.synchronize()
     pairs = 0
     t0 = time.perf_counter()
@@ -341,18 +370,107 @@ def run_e2e(est, batches, W, K, stream, sc):
     return {"pairs": pairs, "seconds": dt, "h2d": h2d, "d2h": 56}
 
 
+def run_batched(args, rank, world, local, dist):
+    import torch
+
+    from paper_2504_04411_gb300 import autotune, ppm, synth
+    W, K = args.warmup, args.steps
+    scenes = synth.batch_scenes(256, seed=synth.SEED_BASE + 3 + 1000 * rank)
+    hps = [s.hitpoints("cuda") for s in scenes]
+    its = [[s.photons(i, "cuda") for s in scenes] for i in range(1, W + K + 1)]
+    torch.cuda.synchronize()
+    if args.mapping is not None and args.cell_factor is not None:
+        tuned = {"mapping": args.mapping, "cell_factors": [args.cell_factor] * len(scenes)}
+    else:
+        tuned = autotune.tune_batch(scenes, hps, its[:3])
+    params = ppm.ppm_default_params()
+    params.mapping = tuned["mapping"]
+    b = ppm.Batch(hps, [s.r0 for s in scenes], [s.J for s in scenes], params=params,
+                  cell_factors=tuned["cell_factors"])
+    for i in range(W):
+        b.step(its[i])
+    torch.cuda.synchronize()
+    tot0 = sum(s.pairs_total for s in b.stats())
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    gms = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    for i in range(K):
+        ev[i][0].record(stream)
+        b.step(its[W + i])
+        ev[i][1].record(stream)
+        if i == K - 1:
+            break
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    st = b.stats()
+    pairs = sum(s.pairs_total for s in st) - tot0
+    total_s = sum(a.elapsed_time(c) for a, c in ev) / 1e3
+    launches = st[0].launches
+    total_s, all_pairs = _reduce(dist, total_s, pairs)
+    value = all_pairs / total_s
+    cand_last = sum(s.candidates for s in st)
+    pairs_last = sum(s.pairs for s in st)
+    gather_ms = st[0].gather_ms
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    roof, other = roofline(gather_ms, sum(s.J for s in scenes), sum(s.nh for s in scenes), cand_last,
+                           pairs_last, sm_count, "k_batch_gather")
+    roof["traffic"] = other["traffic"] = None
+    b.close()
+    # the same problems and photons as separate contexts (the plain method)
+    ests = []
+    for p, s in enumerate(scenes):
+        pp = ppm.ppm_default_params()
+        pp.mapping, pp.cell_factor = tuned["mapping"], tuned["cell_factors"][p]
+        ests.append(ppm.Estimator(hps[p], s.r0, 0.75, pp))
+    for i in range(W):
+        for p, e in enumerate(ests):
+            e.step(its[i][p])
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plain_pairs0 = sum(e.stats().pairs_total for e in ests)
+    a0.record(stream)
+    for i in range(W, W + K):
+        for p, e in enumerate(ests):
+            e.step(its[i][p])
+    a1.record(stream)
+    torch.cuda.synchronize()
+    plain_s = a0.elapsed_time(a1) / 1e3
+    plain_pairs = sum(e.stats().pairs_total for e in ests) - plain_pairs0
+    for e in ests:
+        e.close()
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": 1e3 * total_s / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched: 256 independent problems, hit points log-uniform 1k-256k, "
+                                   "photons/iter log-uniform 10k-1M, 1-3 random unit squares each with "
+                                   "Gaussian lobes and step-edge shadows, ~150 photons per disk",
+                       "hit_points": sum(s.nh for s in scenes), "photons_per_iter": sum(s.J for s in scenes),
+                       "l2": "inputs larger than L2", "parallelism": "single GPU, one persistent launch",
+                       "mapping": tuned["mapping"], "cuda_graph": True},
+            "iterations_per_sec": K / total_s, "gather_ms": gather_ms, "gpu_launches": launches * K,
+            "roofline": roof, "roofline_other": other, "clocks": clk,
+            "vs_plain": {"value": plain_pairs / plain_s, "unit": UNIT,
+                         "speedup": value / (plain_pairs / plain_s),
+                         "equal_mse": "bit-identical state and radiance per problem (tested)"}}
+
+
 def run_reference(args):
     """The oracle as it stands on the host cores, on the same config, one
     bounded sample of hit points per step against the step's photons."""
-    import numpy as np
-
     from paper_2504_04411_gb300 import synth
+    if args.config == "batched":
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "the oracle has no batched form; use --config frame"}), flush=True)
+        return 0
     sc, desc = make_scene(args.config, 0)
     hp_np = sc.hitpoints("cpu").numpy()
     threads = os.cpu_count() or 1
     os.environ.setdefault("OMP_NUM_THREADS", str(threads))
     W, K = args.warmup, args.steps
-    # size the per-step sample so that the whole run stays within minutes
     ph_np = synth.stack_numpy([sc.photons(1, "cpu")])
     _, dt = oracle_sample(sc, ph_np, hp_np, 64, seed=0)
     per_step_s = min(2.0, 150.0 / (W + K))

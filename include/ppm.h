@@ -120,7 +120,8 @@ typedef struct {
     float r_max;           /* largest radius after the update */
     float cell;            /* grid cell edge used by the last build */
     int32_t launches;      /* kernels launched by the last build + gather */
-    int32_t pad;
+    float gather_ms;       /* batches: device time of the last gather launch
+                              (events recorded around it); contexts: -1 */
 } ppm_iter_stats;
 
 /* State per hit point, in the caller's hit-point order (device pointers;
@@ -197,6 +198,49 @@ int ppm_f_critical(int64_t J, double alpha_f, int32_t t_max, double* out, void* 
  * scratch cannot be allocated. */
 int ppm_sort_pairs(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
                    uint32_t* vals_out, int64_t n, int32_t bits, void* stream);
+
+/* ---- batches: many independent problems per launch --------------------
+ * A batch holds n_problems independent problem instances (hit points,
+ * radii, per-iteration photons, window statistics, estimates), each
+ * exactly as one context would hold it: for the same mapping and cell
+ * factor a problem's results are bit-identical to a context's.  One
+ * iteration of all of them is one grid build over all photons (the
+ * problem id is mixed into the bucket hash and checked in the gather) and
+ * ONE persistent gather launch whose resident blocks pull 128-hit-point
+ * tiles from an atomic queue, heaviest problems first.  From the second
+ * iteration on, the whole iteration is replayed as a CUDA graph on a
+ * private stream ordered after the caller's stream. */
+typedef struct ppm_batch ppm_batch;
+
+/* hp: n_problems hit-point sets (device arrays as for ppm_create); r0:
+ * n_problems initial radii (host); J: n_problems light paths per iteration
+ * (host) -- every iteration problem p must bring exactly J[p] photons;
+ * cell_factor: n_problems grid cell factors in [0.5, 4] (host; from the
+ * autotuner) or NULL for params->cell_factor.  Normals: for every problem
+ * or for none.  Synchronizes the stream; copies the hit points. */
+int ppm_batch_create(int32_t n_problems, const ppm_hitpoints* hp, const float* r0,
+                     const int64_t* J, float alpha, const ppm_params* params,
+                     const float* cell_factor, void* stream, ppm_batch** out);
+
+/* Iteration iter (previous + 1, from 1) of every problem; ph: n_problems
+ * photon sets.  The photon arrays are read by work ordered after the
+ * caller's stream at the time of the call and must stay valid until the
+ * caller's stream passes this call. */
+int ppm_batch_iterate(ppm_batch* b, const ppm_photons* ph, int32_t iter);
+
+/* Radiance of one problem into out (device, that problem's n or n x 3). */
+int ppm_batch_radiance(ppm_batch* b, int32_t problem, float* out);
+
+/* State of one problem (as ppm_get_state); waits. */
+int ppm_batch_get_state(ppm_batch* b, int32_t problem, const ppm_state_view* v);
+
+/* Counters of the last iteration, one entry per problem; waits. */
+int ppm_batch_stats(ppm_batch* b, ppm_iter_stats* out);
+
+/* 1 once the iteration has been captured into a CUDA graph, else 0. */
+int ppm_batch_graph_ready(ppm_batch* b);
+
+void ppm_batch_destroy(ppm_batch* b);
 
 /* Frees everything the context owns (waits for the stream first). */
 void ppm_destroy(ppm_ctx* ctx);

@@ -216,6 +216,42 @@ void free_ctx(ppm_ctx* c)
 
 }  // namespace
 
+int ppm_prepare_hitpoints(const ppm_hitpoints* hp, bool with_rho, uint32_t* orig, float4* pos,
+                          float4* u, float4* v, cudaStream_t st)
+{
+    const int64_t n = hp->n;
+    if (n <= 0) return PPM_OK;
+    // spatial order: 30-bit Hilbert index of the position in the hit
+    // points' bounding box, stable radix sort
+    SortScratch hs;
+    uint32_t* bb = nullptr;
+    if (!dalloc(&bb, 6)) return PPM_ENOMEM;
+    int rc = PPM_OK;
+    const uint32_t init[6] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u};
+    if (cudaMemcpyAsync(bb, init, sizeof(init), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        rc = PPM_ECUDA;
+    if (rc == PPM_OK) rc = ppm_sort_scratch_reserve(&hs, n);
+    if (rc == PPM_OK) {
+        const unsigned nb = (unsigned)((n + 255) / 256);
+        k_bbox<<<nb, 256, 0, st>>>(n, hp->pos, bb);
+        k_morton<<<nb, 256, 0, st>>>(n, hp->pos, bb, hs.keys, hs.vals);
+        rc = ppm_radix_sort_pairs(&hs, n, 30, st);
+        if (rc == PPM_OK) {
+            k_hp_permute<<<nb, 256, 0, st>>>(n, hs.vals, hp->pos, hp->u, hp->v, hp->nq,
+                                             with_rho ? hp->rho : nullptr, orig, pos, u, v);
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) {
+                ppm_note_cuda_error(e, "hit-point preparation", __FILE__, __LINE__);
+                rc = PPM_ECUDA;
+            }
+        }
+    }
+    cudaFree(bb);
+    ppm_sort_scratch_free(&hs);
+    return rc;
+}
+
 extern "C" {
 
 void ppm_default_params(ppm_params* p)
@@ -249,6 +285,7 @@ const char* ppm_strerror(int code)
 int ppm_create(const ppm_hitpoints* hp, float r0, float alpha, const ppm_params* params,
                void* stream, ppm_ctx** out)
 {
+    PPM_ENTRY();
     if (!out) return PPM_EINVAL;
     *out = nullptr;
     if (!hp || hp->n < 0 || hp->n > 0x7fffffffll) return PPM_EINVAL;
@@ -289,32 +326,9 @@ int ppm_create(const ppm_hitpoints* hp, float r0, float alpha, const ppm_params*
     int rc = PPM_OK;
     do {
         if (n > 0) {
-            // spatial order: 30-bit Hilbert index of the position in the
-            // hit points' bounding box, stable radix sort
-            SortScratch hs;
-            uint32_t* bb = nullptr;
-            if (!dalloc(&bb, 6)) { rc = PPM_ENOMEM; break; }
-            uint32_t init[6] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u};
-            if (cudaMemcpyAsync(bb, init, sizeof(init), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-                (rc = ppm_sort_scratch_reserve(&hs, n)) != PPM_OK) {
-                cudaFree(bb); ppm_sort_scratch_free(&hs);
-                rc = rc ? rc : PPM_ECUDA;
-                break;
-            }
-            const unsigned nb = (unsigned)((n + 255) / 256);
-            k_bbox<<<nb, 256, 0, st>>>(n, hp->pos, bb);
-            k_morton<<<nb, 256, 0, st>>>(n, hp->pos, bb, hs.keys, hs.vals);
-            rc = ppm_radix_sort_pairs(&hs, n, 30, st);
-            if (rc == PPM_OK) {
-                k_hp_permute<<<nb, 256, 0, st>>>(n, hs.vals, hp->pos, hp->u, hp->v, hp->nq,
-                                                 prm.vcm ? hp->rho : nullptr, c->hp_orig,
-                                                 c->hp_pos, c->hp_u, c->hp_v);
-                if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
-                    rc = PPM_ECUDA;
-            }
-            cudaFree(bb);
-            ppm_sort_scratch_free(&hs);
+            rc = ppm_prepare_hitpoints(hp, prm.vcm != 0, c->hp_orig, c->hp_pos, c->hp_u, c->hp_v, st);
             if (rc) break;
+            const unsigned nb = (unsigned)((n + 255) / 256);
             k_fill_f32<<<nb, 256, 0, st>>>(n, c->r, r0);
         }
         if (cudaMemsetAsync(c->t, 0, n * sizeof(int32_t), st) != cudaSuccess ||
@@ -343,6 +357,7 @@ int ppm_set_stream(ppm_ctx* c, void* stream)
 
 int ppm_build_grid(ppm_ctx* c, const ppm_photons* ph)
 {
+    PPM_ENTRY();
     if (!c || !ph || ph->n < 0 || ph->n > 0xfffffff0ll || ph->J < 2) return PPM_EINVAL;
     if (ph->channels != c->nch) return PPM_EINVAL;
     if (ph->n > 0 && (!ph->pos || !ph->flux)) return PPM_EINVAL;
@@ -360,6 +375,7 @@ int ppm_build_grid(ppm_ctx* c, const ppm_photons* ph)
 
 int ppm_gather_test_update(ppm_ctx* c, int32_t iter)
 {
+    PPM_ENTRY();
     if (!c) return PPM_EINVAL;
     if (iter != c->iter + 1 || !c->grid_valid) return PPM_ESTATE;
     int launches = c->launches_build + (c->nh > 0 ? 1 : 0);
@@ -380,12 +396,14 @@ int ppm_gather_test_update(ppm_ctx* c, int32_t iter)
 
 int ppm_radiance(ppm_ctx* c, float* out)
 {
+    PPM_ENTRY();
     if (!c || (!out && c->nh > 0)) return PPM_EINVAL;
     return ppm_radiance_launch(c, out);
 }
 
 int ppm_get_state(ppm_ctx* c, const ppm_state_view* v)
 {
+    PPM_ENTRY();
     if (!c || !v) return PPM_EINVAL;
     if (c->nh > 0) {
         k_state_io<true><<<(unsigned)((c->nh + 255) / 256), 256, 0, c->stream>>>(
@@ -398,6 +416,7 @@ int ppm_get_state(ppm_ctx* c, const ppm_state_view* v)
 
 int ppm_set_state(ppm_ctx* c, const ppm_state_view* v)
 {
+    PPM_ENTRY();
     if (!c || !v) return PPM_EINVAL;
     if (c->nh > 0) {
         const unsigned nb = (unsigned)((c->nh + 255) / 256);
@@ -424,6 +443,7 @@ int ppm_set_iteration(ppm_ctx* c, int32_t iter)
 
 int ppm_stats(ppm_ctx* c, ppm_iter_stats* out)
 {
+    PPM_ENTRY();
     if (!c || !out) return PPM_EINVAL;
     unsigned long long cnt[4];
     float rm;
@@ -444,11 +464,13 @@ int ppm_stats(ppm_ctx* c, ppm_iter_stats* out)
     out->r_max = rm;
     out->cell = g.h;
     out->launches = c->launches_iter;
+    out->gather_ms = -1.f;
     return PPM_OK;
 }
 
 int ppm_f_critical(int64_t J, double alpha_f, int32_t t_max, double* out, void* stream)
 {
+    PPM_ENTRY();
     if (J < 2 || !(alpha_f > 0.0 && alpha_f < 1.0) || t_max < 1 || !out) return PPM_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     PPM_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
@@ -458,6 +480,7 @@ int ppm_f_critical(int64_t J, double alpha_f, int32_t t_max, double* out, void* 
 int ppm_sort_pairs(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
                    uint32_t* vals_out, int64_t n, int32_t bits, void* stream)
 {
+    PPM_ENTRY();
     if (n < 0 || n >= 0xffffffffll || bits < 1 || bits > 32) return PPM_EINVAL;
     if (n > 0 && (!keys_in || !vals_in || !keys_out || !vals_out)) return PPM_EINVAL;
     if (n == 0) return PPM_OK;

@@ -23,6 +23,8 @@ __global__ void k_grid_geom(GridGeom* __restrict__ g, const float* __restrict__ 
     o.inv_h = __frcp_rn(h);
     o.tmask = tmask;
     o.lb = lb;
+    o.pid = 0u;
+    o.pad[0] = o.pad[1] = o.pad[2] = 0u;
     *g = o;
 }
 
@@ -132,7 +134,7 @@ int reserve_photons(ppm_ctx* c, int64_t n)
 // Bucket-table size: T = 2^tbits >= 2 n (so an empty cell lands on an
 // occupied bucket with probability <= 1/2 per photon-bucket), and at least
 // 4 blocks of B^3 cells.
-static int table_bits(int64_t n, int lb)
+int ppm_table_bits(int64_t n, int lb)
 {
     int b = 3 * lb + 2;
     while (b < 30 && ((int64_t)1 << b) < 2 * n) ++b;
@@ -147,7 +149,7 @@ int ppm_grid_build(ppm_ctx* c, const ppm_photons* ph)
     // hash blocks of 4^3 cells suffice for one sphere (<= 4 cells per axis at
     // cell_factor >= 1); the warp-union traversal and cell_factor < 1 need 8^3
     const int lb = (c->prm.cell_factor >= 1.0f && c->prm.mapping == 0) ? 2 : 3;
-    c->tbits = table_bits(n, lb);
+    c->tbits = ppm_table_bits(n, lb);
     const uint32_t T = 1u << c->tbits;
     if ((int64_t)T + 1 > c->cs_cap) {
         cudaFree(c->cell_start);
@@ -177,22 +179,42 @@ int ppm_grid_build(ppm_ctx* c, const ppm_photons* ph)
         rc = ppm_radix_sort_pairs(&c->sort, n, c->tbits, c->stream);
         if (rc) return rc;
     }
-    k_cell_start<<<(unsigned)((n + 1 + 255) / 256), 256, 0, c->stream>>>(c->sort.keys, n, T, c->cell_start);
-    PPM_LAUNCH_CHECK();
+    rc = ppm_cell_start_launch(c->sort.keys, n, T, c->cell_start, c->stream);
+    if (rc) return rc;
     if (n > 0) {
-        const unsigned nb = (unsigned)((n + 255) / 256);
         const bool rec1 = c->nch == 3 || vcm;
-        if (rec1 && aux)
-            k_permute<true, true><<<nb, 256, 0, c->stream>>>(n, c->sort.vals, c->pack0, c->pack1, c->pack_aux, c->rec0, c->rec1, c->aux);
-        else if (rec1)
-            k_permute<true, false><<<nb, 256, 0, c->stream>>>(n, c->sort.vals, c->pack0, c->pack1, c->pack_aux, c->rec0, c->rec1, c->aux);
-        else if (aux)
-            k_permute<false, true><<<nb, 256, 0, c->stream>>>(n, c->sort.vals, c->pack0, c->pack1, c->pack_aux, c->rec0, c->rec1, c->aux);
-        else
-            k_permute<false, false><<<nb, 256, 0, c->stream>>>(n, c->sort.vals, c->pack0, c->pack1, c->pack_aux, c->rec0, c->rec1, c->aux);
-        PPM_LAUNCH_CHECK();
+        rc = ppm_permute_launch(n, c->sort.vals, c->pack0, rec1 ? c->pack1 : nullptr,
+                                aux ? c->pack_aux : nullptr, c->rec0, rec1 ? c->rec1 : nullptr,
+                                aux ? c->aux : nullptr, c->stream);
+        if (rc) return rc;
     }
     c->n_ph = n;
     c->launches_build = 2 + (n > 0 ? 2 + 5 * ((c->tbits + 7) / 8) : 0);
+    return PPM_OK;
+}
+
+int ppm_cell_start_launch(const uint32_t* keys, int64_t n, uint32_t T, uint32_t* cell_start,
+                          cudaStream_t st)
+{
+    k_cell_start<<<(unsigned)((n + 1 + 255) / 256), 256, 0, st>>>(keys, n, T, cell_start);
+    PPM_LAUNCH_CHECK();
+    return PPM_OK;
+}
+
+int ppm_permute_launch(int64_t n, const uint32_t* vals, const float4* pack0, const float4* pack1,
+                       const uint4* pack_aux, float4* rec0, float4* rec1, uint4* aux,
+                       cudaStream_t st)
+{
+    if (n <= 0) return PPM_OK;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    if (rec1 && aux)
+        k_permute<true, true><<<nb, 256, 0, st>>>(n, vals, pack0, pack1, pack_aux, rec0, rec1, aux);
+    else if (rec1)
+        k_permute<true, false><<<nb, 256, 0, st>>>(n, vals, pack0, pack1, pack_aux, rec0, rec1, aux);
+    else if (aux)
+        k_permute<false, true><<<nb, 256, 0, st>>>(n, vals, pack0, pack1, pack_aux, rec0, rec1, aux);
+    else
+        k_permute<false, false><<<nb, 256, 0, st>>>(n, vals, pack0, pack1, pack_aux, rec0, rec1, aux);
+    PPM_LAUNCH_CHECK();
     return PPM_OK;
 }

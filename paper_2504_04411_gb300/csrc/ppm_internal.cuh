@@ -8,12 +8,17 @@
 
 #define PPM_NG 12
 
-// Return PPM_ECUDA from the enclosing function if a runtime call fails.
+// Return PPM_ECUDA from the enclosing function if a runtime call fails
+// (the thread's last-error slot is cleared so later checks are not fooled).
 #define PPM_CUDA(call)                                                       \
     do {                                                                     \
         cudaError_t e_ = (call);                                             \
-        if (e_ != cudaSuccess) { ppm_note_cuda_error(e_, #call, __FILE__, __LINE__); return PPM_ECUDA; } \
+        if (e_ != cudaSuccess) { ppm_note_cuda_error(e_, #call, __FILE__, __LINE__); cudaGetLastError(); return PPM_ECUDA; } \
     } while (0)
+
+// Launch checks read the thread's last-error slot, which other code in the
+// process may have left set: every entry point clears it first.
+#define PPM_ENTRY() ((void)cudaGetLastError())
 
 #define PPM_LAUNCH_CHECK()                                                   \
     do {                                                                     \
@@ -39,6 +44,8 @@ struct GridGeom {
     float h;           // cell edge
     uint32_t tmask;    // T - 1
     int32_t lb;        // log2 of the block edge in cells (2 or 3)
+    uint32_t pid;      // problem id mixed into the hash (0 for one problem)
+    uint32_t pad[3];
 };
 
 __device__ __forceinline__ uint32_t ppm_fmix32(uint32_t x)
@@ -63,7 +70,8 @@ __device__ __forceinline__ uint32_t ppm_bucket(int ix, int iy, int iz, const Gri
     const uint32_t m = (1u << lb) - 1u;
     uint32_t local = ((uint32_t)ix & m) | (((uint32_t)iy & m) << lb) | (((uint32_t)iz & m) << (2 * lb));
     uint32_t bx = (uint32_t)(ix >> lb), by = (uint32_t)(iy >> lb), bz = (uint32_t)(iz >> lb);
-    uint32_t hb = ppm_fmix32(bx * 0x9E3779B1u ^ ppm_fmix32(by * 0x85EBCA77u ^ ppm_fmix32(bz + 0x27D4EB2Fu)));
+    uint32_t hb = ppm_fmix32(bx * 0x9E3779B1u ^ ppm_fmix32(by * 0x85EBCA77u ^
+                              ppm_fmix32(bz + 0x27D4EB2Fu + g.pid * 0x632BE59Bu)));
     return ((hb << (3 * lb)) | local) & g.tmask;
 }
 
@@ -169,5 +177,17 @@ struct ppm_ctx {
 
 // ppm_grid.cu / ppm_gather.cu
 int ppm_grid_build(ppm_ctx* c, const ppm_photons* ph);
+// bucket-table size for n photons and hash blocks of 2^lb cells per axis
+int ppm_table_bits(int64_t n, int lb);
+// cell_start[b] = first sorted photon with bucket >= b, b in [0, T]
+int ppm_cell_start_launch(const uint32_t* keys, int64_t n, uint32_t T, uint32_t* cell_start,
+                          cudaStream_t st);
+// packed records gathered into sorted order (rec1 / aux when non-NULL)
+int ppm_permute_launch(int64_t n, const uint32_t* vals, const float4* pack0, const float4* pack1,
+                       const uint4* pack_aux, float4* rec0, float4* rec1, uint4* aux,
+                       cudaStream_t st);
+// ppm_api.cu: hit points -> Hilbert-sorted internal layout (synchronizes st)
+int ppm_prepare_hitpoints(const ppm_hitpoints* hp, bool with_rho, uint32_t* orig, float4* pos,
+                          float4* u, float4* v, cudaStream_t st);
 int ppm_gather_launch(ppm_ctx* c, float bound);
 int ppm_radiance_launch(ppm_ctx* c, float* out);

@@ -64,6 +64,7 @@ extern "C" int ppm_sort_pairs_noalloc(const uint32_t* keys_in, const uint32_t* v
                                       uint32_t* keys_out, uint32_t* vals_out, int64_t n,
                                       int32_t bits, void* stream)
 {
+    PPM_ENTRY();
     if (n < 0 || n > kMaxPairs || bits < 1 || bits > 32) return PPM_EINVAL;
     if (n > 0 && (!keys_in || !vals_in || !keys_out || !vals_out)) return PPM_EINVAL;
     uint32_t* scratch = nullptr;

@@ -46,7 +46,7 @@ class ppm_iter_stats(ctypes.Structure):
                 ("pairs", ctypes.c_int64), ("candidates", ctypes.c_int64),
                 ("rejects", ctypes.c_int64), ("pairs_total", ctypes.c_int64),
                 ("r_max", ctypes.c_float), ("cell", ctypes.c_float),
-                ("launches", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("launches", ctypes.c_int32), ("gather_ms", ctypes.c_float)]
 
 
 class ppm_state_view(ctypes.Structure):
@@ -58,7 +58,10 @@ class ppm_state_view(ctypes.Structure):
 EXPORTS = ("ppm_default_params", "ppm_create", "ppm_set_stream", "ppm_build_grid",
            "ppm_gather_test_update", "ppm_radiance", "ppm_get_state", "ppm_set_state",
            "ppm_set_iteration", "ppm_stats", "ppm_f_critical", "ppm_sort_pairs",
-           "ppm_destroy", "ppm_strerror", "ppm_sort_pairs_noalloc")
+           "ppm_destroy", "ppm_strerror", "ppm_sort_pairs_noalloc",
+           "ppm_batch_create", "ppm_batch_iterate", "ppm_batch_radiance",
+           "ppm_batch_get_state", "ppm_batch_stats", "ppm_batch_graph_ready",
+           "ppm_batch_destroy")
 
 _lib = None
 
@@ -98,6 +101,22 @@ def load(path: str = LIB_PATH):
     L.ppm_sort_pairs.argtypes = [c_p, c_p, c_p, c_p, ctypes.c_int64, ctypes.c_int32, c_p]
     L.ppm_sort_pairs_noalloc.restype = ctypes.c_int
     L.ppm_sort_pairs_noalloc.argtypes = [c_p, c_p, c_p, c_p, ctypes.c_int64, ctypes.c_int32, c_p]
+    L.ppm_batch_create.restype = ctypes.c_int
+    L.ppm_batch_create.argtypes = [ctypes.c_int32, ctypes.POINTER(ppm_hitpoints), c_p, c_p,
+                                   ctypes.c_float, ctypes.POINTER(ppm_params), c_p, c_p,
+                                   ctypes.POINTER(c_p)]
+    L.ppm_batch_iterate.restype = ctypes.c_int
+    L.ppm_batch_iterate.argtypes = [c_p, ctypes.POINTER(ppm_photons), ctypes.c_int32]
+    L.ppm_batch_radiance.restype = ctypes.c_int
+    L.ppm_batch_radiance.argtypes = [c_p, ctypes.c_int32, c_p]
+    L.ppm_batch_get_state.restype = ctypes.c_int
+    L.ppm_batch_get_state.argtypes = [c_p, ctypes.c_int32, ctypes.POINTER(ppm_state_view)]
+    L.ppm_batch_stats.restype = ctypes.c_int
+    L.ppm_batch_stats.argtypes = [c_p, ctypes.POINTER(ppm_iter_stats)]
+    L.ppm_batch_graph_ready.restype = ctypes.c_int
+    L.ppm_batch_graph_ready.argtypes = [c_p]
+    L.ppm_batch_destroy.restype = None
+    L.ppm_batch_destroy.argtypes = [c_p]
     L.ppm_destroy.restype = None
     L.ppm_destroy.argtypes = [c_p]
     L.ppm_strerror.restype = ctypes.c_char_p
@@ -275,3 +294,104 @@ class Estimator:
                 self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- batches ---
+def ppm_batch_create(hps, r0s, Js, alpha: float = 0.75, params: ppm_params | None = None,
+                     cell_factors=None, stream=None) -> ctypes.c_void_p:
+    """hps: list of HitPoints-like objects (pos, u, v, nq, rho CUDA tensors)."""
+    import numpy as np
+    P = len(hps)
+    vcm = bool(params.vcm) if params is not None else False
+    arr = (ppm_hitpoints * P)()
+    for i, hp in enumerate(hps):
+        arr[i] = ppm_hitpoints(hp.pos.shape[0], _ptr(hp.pos), _ptr(hp.u), _ptr(hp.v), _ptr(hp.nq),
+                               _ptr(hp.rho) if vcm else None)
+    r0 = np.ascontiguousarray(r0s, np.float32)
+    J = np.ascontiguousarray(Js, np.int64)
+    cf = None if cell_factors is None else np.ascontiguousarray(cell_factors, np.float32)
+    b = ctypes.c_void_p()
+    _check("ppm_batch_create", load().ppm_batch_create(
+        P, arr, r0.ctypes.data_as(c_p), J.ctypes.data_as(c_p), alpha,
+        ctypes.byref(params) if params is not None else None,
+        None if cf is None else cf.ctypes.data_as(c_p), _stream(stream), ctypes.byref(b)))
+    return b
+
+
+def ppm_batch_iterate(b, photons, it: int, vcm: bool = False) -> None:
+    """photons: list (one per problem) of Photons-like objects."""
+    P = len(photons)
+    arr = (ppm_photons * P)()
+    for i, ph in enumerate(photons):
+        ch = 3 if ph.flux.dim() == 2 else 1
+        n = ph.pos.shape[0]
+        arr[i] = ppm_photons(n, n, _ptr(ph.pos), _ptr(ph.flux), ch, 0, _ptr(ph.nq),
+                             _ptr(ph.rho) if vcm else None, _ptr(ph.wq) if vcm else None)
+    _check("ppm_batch_iterate", load().ppm_batch_iterate(b, arr, it))
+
+
+def ppm_batch_radiance(b, problem: int, out) -> None:
+    _check("ppm_batch_radiance", load().ppm_batch_radiance(b, problem, _ptr(out)))
+
+
+def ppm_batch_get_state(b, problem: int, r=None, t=None, counts=None, S=None, Q=None, tau=None,
+                        F=None) -> None:
+    v = ppm_state_view(_ptr(r), _ptr(t), _ptr(counts), _ptr(S), _ptr(Q), _ptr(tau), _ptr(F))
+    _check("ppm_batch_get_state", load().ppm_batch_get_state(b, problem, ctypes.byref(v)))
+
+
+def ppm_batch_stats(b, n_problems: int):
+    arr = (ppm_iter_stats * n_problems)()
+    _check("ppm_batch_stats", load().ppm_batch_stats(b, arr))
+    return list(arr)
+
+
+def ppm_batch_graph_ready(b) -> bool:
+    return bool(load().ppm_batch_graph_ready(b))
+
+
+def ppm_batch_destroy(b) -> None:
+    if b:
+        load().ppm_batch_destroy(b)
+
+
+class Batch:
+    """Owns one batch; `step(photon_lists)` runs one iteration of all problems."""
+
+    def __init__(self, hps, r0s, Js, alpha: float = 0.75, params: ppm_params | None = None,
+                 cell_factors=None, stream=None):
+        self.params = params if params is not None else ppm_default_params()
+        self.P = len(hps)
+        self.ns = [int(h.pos.shape[0]) for h in hps]
+        self.channels = int(self.params.channels)
+        self.ntc = 3 if self.params.rgb_test else 1
+        self.b = ppm_batch_create(hps, r0s, Js, alpha, self.params, cell_factors, stream)
+        self.it = 0
+
+    def step(self, photons) -> None:
+        self.it += 1
+        ppm_batch_iterate(self.b, photons, self.it, vcm=bool(self.params.vcm))
+
+    def radiance(self, p: int) -> torch.Tensor:
+        shape = (self.ns[p],) if self.channels == 1 else (self.ns[p], 3)
+        out = torch.empty(shape, device="cuda", dtype=torch.float32)
+        ppm_batch_radiance(self.b, p, out)
+        return out
+
+    def state(self, p: int) -> dict:
+        n, d = self.ns[p], "cuda"
+        st = {"r": torch.empty(n, device=d), "t": torch.empty(n, device=d, dtype=torch.int32),
+              "counts": torch.empty(n, PPM_NGROUPS, device=d, dtype=torch.int32),
+              "S": torch.empty(n, self.ntc, PPM_NGROUPS, device=d),
+              "Q": torch.empty(n, self.ntc, PPM_NGROUPS, device=d),
+              "tau": torch.empty(n, self.channels, device=d, dtype=torch.float64),
+              "F": torch.empty(n, device=d)}
+        ppm_batch_get_state(self.b, p, **st)
+        return st
+
+    def stats(self):
+        return ppm_batch_stats(self.b, self.P)
+
+    def close(self) -> None:
+        ppm_batch_destroy(self.b)
+        self.b = None

@@ -308,3 +308,141 @@ class BoxScene:
             dens = dens + torch.where(face == L["face"], L["w"] * gpdf,
                                       torch.zeros_like(gpdf))
         return dens * (~self._shadowed(face, a.float(), b.float())).double()
+
+
+# --------------------------------------------------------------------------
+# random-orientation unit squares (one problem of a batch)
+# --------------------------------------------------------------------------
+def onb_from_normal(n: torch.Tensor):
+    """Tangent frame (t, b) of unit normals n (..., 3): the branchless
+    construction of Duff et al., "Building an Orthonormal Basis, Revisited"
+    (JCGT 2017), evaluated in float64."""
+    n = n.double()
+    sign = torch.where(n[..., 2] >= 0, torch.ones_like(n[..., 2]), -torch.ones_like(n[..., 2]))
+    a = -1.0 / (sign + n[..., 2])
+    b = n[..., 0] * n[..., 1] * a
+    t = torch.stack([1.0 + sign * n[..., 0] * n[..., 0] * a, sign * b, -sign * n[..., 0]], -1)
+    bb = torch.stack([b, sign + n[..., 1] * n[..., 1] * a, -n[..., 1]], -1)
+    return t, bb
+
+
+@dataclass
+class SquaresScene:
+    """1-3 unit squares with random orientation and position, hit points on a
+    jittered grid per square, photons uniform over the squares plus Gaussian
+    lobes (peak 20x) and step-edge shadows, flux 1/J; r0 chosen for ~150
+    expected photons per disk on the uniform part."""
+    nh: int = 4000
+    J: int = 40_000
+    n_squares: int = 2
+    n_lobes: int = 2
+    n_shadows: int = 2
+    lobe_peak: float = 20.0
+    photons_per_disk: float = 150.0
+    seed: int = SEED_BASE + 2
+
+    def __post_init__(self):
+        g = _gen(self.seed, -1, "cpu")
+        R = lambda *s: torch.rand(*s, generator=g, dtype=torch.float64)
+        nrm = torch.randn(self.n_squares, 3, generator=g, dtype=torch.float64)
+        self.normal = nrm / nrm.norm(dim=1, keepdim=True)
+        self.t, self.b = onb_from_normal(self.normal)
+        self.center = (R(self.n_squares, 3) - 0.5) * 3.0
+        self.lobes = []
+        for _ in range(self.n_lobes):
+            sq = int(torch.randint(0, self.n_squares, (1,), generator=g))
+            c = (0.25 + 0.5 * R(2) - 0.5).tolist()
+            s1, s2 = (0.005 + 0.015 * R(2)).tolist()
+            self.lobes.append({"sq": sq, "c": c, "s": (s1, s2), "th": float(R(1)) * math.pi})
+        self.shadows = []
+        for k in range(self.n_shadows):
+            sq = int(torch.randint(0, self.n_squares, (1,), generator=g))
+            if k % 2 == 0:
+                p = (0.3 + 0.4 * R(2) - 0.5).tolist()
+                a = float(R(1)) * 2 * math.pi
+                self.shadows.append({"sq": sq, "kind": "half", "p": p, "n": (math.cos(a), math.sin(a))})
+            else:
+                lo = (0.2 + 0.4 * R(2) - 0.5).tolist()
+                ext = (0.1 + 0.2 * R(2)).tolist()
+                self.shadows.append({"sq": sq, "kind": "rect", "lo": lo,
+                                     "hi": [lo[0] + ext[0], lo[1] + ext[1]]})
+        area = float(self.n_squares)
+        wl = [self.lobe_peak * (1.0 / area) * 2 * math.pi * L["s"][0] * L["s"][1] for L in self.lobes]
+        tot = 1.0 + sum(wl)
+        self.w_uniform = 1.0 / tot
+        for L, w in zip(self.lobes, wl):
+            L["w"] = w / tot
+        self.r0 = float(math.sqrt(self.photons_per_disk * area / (math.pi * self.J)))
+
+    def _embed(self, sq, a, b):
+        c = self.center.to(a.device)[sq]
+        t = self.t.to(a.device)[sq]
+        bb = self.b.to(a.device)[sq]
+        return (c + a.double()[:, None] * t + b.double()[:, None] * bb).float()
+
+    def hitpoints(self, device="cpu") -> HitPoints:
+        g = _gen(self.seed, -2, device)
+        per = [self.nh // self.n_squares + (1 if q < self.nh % self.n_squares else 0)
+               for q in range(self.n_squares)]
+        sqs, As, Bs = [], [], []
+        for q, nq in enumerate(per):
+            nx = max(1, int(round(math.sqrt(nq))))
+            ny = (nq + nx - 1) // nx
+            idx = torch.arange(nq, device=device)
+            j = torch.rand(nq, 2, generator=g, device=device, dtype=torch.float64)
+            As.append(((idx % nx).double() + j[:, 0]) / nx - 0.5)
+            Bs.append(((idx // nx).double() + j[:, 1]) / ny - 0.5)
+            sqs.append(torch.full((nq,), q, device=device, dtype=torch.int64))
+        sq = torch.cat(sqs)
+        pos = self._embed(sq, torch.cat(As), torch.cat(Bs))
+        u = self.t.to(device)[sq].float().contiguous()
+        v = self.b.to(device)[sq].float().contiguous()
+        nq = pack_snorm8(self.normal.to(device)[sq])
+        return HitPoints(pos.contiguous(), u, v, nq, None, sq)
+
+    def photons(self, it: int, device="cpu") -> Photons:
+        g = _gen(self.seed, it, device)
+        J = self.J
+        w = torch.tensor([self.w_uniform] + [L["w"] for L in self.lobes], dtype=torch.float64)
+        cdf = torch.cumsum(w, 0) / w.sum()
+        comp = torch.searchsorted(cdf.to(device), torch.rand(J, generator=g, device=device,
+                                                             dtype=torch.float64)).clamp_max(len(w) - 1)
+        uni = torch.rand(J, 3, generator=g, device=device, dtype=torch.float64)
+        sq = torch.clamp((uni[:, 0] * self.n_squares).long(), max=self.n_squares - 1)
+        a = uni[:, 1] - 0.5
+        b = uni[:, 2] - 0.5
+        gz = torch.randn(J, 2, generator=g, device=device, dtype=torch.float64)
+        for k, L in enumerate(self.lobes):
+            m = comp == (k + 1)
+            c, s_ = math.cos(L["th"]), math.sin(L["th"])
+            x1, x2 = gz[:, 0] * L["s"][0], gz[:, 1] * L["s"][1]
+            a = torch.where(m, L["c"][0] + c * x1 - s_ * x2, a)
+            b = torch.where(m, L["c"][1] + s_ * x1 + c * x2, b)
+            sq = torch.where(m, torch.full_like(sq, L["sq"]), sq)
+        lit = torch.ones(J, dtype=torch.bool, device=device)
+        for S in self.shadows:
+            m = sq == S["sq"]
+            if S["kind"] == "half":
+                d = (a - S["p"][0]) * S["n"][0] + (b - S["p"][1]) * S["n"][1]
+                lit &= ~(m & (d > 0))
+            else:
+                lit &= ~(m & (a >= S["lo"][0]) & (a <= S["hi"][0]) & (b >= S["lo"][1]) & (b <= S["hi"][1]))
+        pos = self._embed(sq, a, b).contiguous()
+        flux = (lit.float() / J).contiguous()
+        return Photons(pos, flux, pack_snorm8(self.normal.to(device)[sq]), None, None)
+
+
+def batch_scenes(n_problems=256, nh_range=(1_000, 256_000), J_range=(10_000, 1_000_000),
+                 seed=SEED_BASE + 3, photons_per_disk=150.0):
+    """Independent problems with log-uniform hit-point and photon counts."""
+    g = _gen(seed, -3, "cpu")
+    u = torch.rand(n_problems, 3, generator=g, dtype=torch.float64)
+    lo_h, hi_h = math.log(nh_range[0]), math.log(nh_range[1])
+    lo_j, hi_j = math.log(J_range[0]), math.log(J_range[1])
+    out = []
+    for p in range(n_problems):
+        nh = int(round(math.exp(lo_h + (hi_h - lo_h) * float(u[p, 0]))))
+        J = int(round(math.exp(lo_j + (hi_j - lo_j) * float(u[p, 1]))))
+        out.append(SquaresScene(nh=nh, J=J, n_squares=1 + int(float(u[p, 2]) * 3),
+                                photons_per_disk=photons_per_disk, seed=seed + 17 * (p + 1)))
+    return out

@@ -1,0 +1,104 @@
+"""Batched persistent launch (many independent problems per iteration,
+replayed as a CUDA graph) through the C ABI: every problem against the
+oracle, and bit-identical to the same problem run as its own context."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2504_04411_gb300 import synth
+
+from parity import compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _params(**kw):
+    from paper_2504_04411_gb300 import ppm
+    p = ppm.ppm_default_params()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def _problems():
+    sizes = [(1500, 12_000), (130, 4_000), (4100, 30_000), (700, 50_000), (2600, 9_000), (1, 2_000)]
+    return [synth.SquaresScene(nh=nh, J=J, n_squares=1 + i % 3, seed=synth.SEED_BASE + 300 + i)
+            for i, (nh, J) in enumerate(sizes)]
+
+
+def _run_batch(scenes, iters, params, cfs=None):
+    import torch
+    from paper_2504_04411_gb300 import ppm
+    hps = [s.hitpoints("cuda") for s in scenes]
+    phs = [[s.photons(i, "cuda") for s in scenes] for i in range(1, iters + 1)]
+    b = ppm.Batch(hps, [s.r0 for s in scenes], [s.J for s in scenes], params=params, cell_factors=cfs)
+    states, stats = [], []
+    graph = []
+    for it in range(iters):
+        b.step(phs[it])
+        states.append([{k: v.cpu().numpy() for k, v in b.state(p).items()} for p in range(len(scenes))])
+        stats.append(b.stats())
+        graph.append(ppm.ppm_batch_graph_ready(b.b))
+    L = [b.radiance(p).cpu().numpy() for p in range(len(scenes))]
+    b.close()
+    torch.cuda.synchronize()
+    return hps, phs, states, stats, L, graph
+
+
+@pytest.mark.parametrize("mapping", [0, 1])
+def test_batch_matches_oracle_per_problem(mapping):
+    scenes = _problems()
+    iters = 4
+    hps, phs, states, stats, L, graph = _run_batch(scenes, iters, _params(mapping=mapping))
+    assert graph == [False, True, True, True]        # captured at the 2nd iteration
+    for p, sc in enumerate(scenes):
+        ref = O.run(hps[p].numpy(), synth.stack_numpy([phs[i][p] for i in range(iters)]), sc.r0, iters)
+        st = [states[i][p] for i in range(iters)]
+        ss = [{"pairs": stats[i][p].pairs, "flags": stats[i][p].flags} for i in range(iters)]
+        rep = compare(st, ss, L[p], ref, iters)
+        assert rep.diverged <= 2
+
+
+@pytest.mark.parametrize("mapping", [0, 1])
+def test_batch_bit_identical_to_single_contexts(mapping):
+    import torch
+    from paper_2504_04411_gb300 import ppm
+    scenes = _problems()
+    iters = 4
+    cfs = [0.5, 1.0, 2.0, 1.0, 0.5, 1.0]
+    hps, phs, states, stats, L, _ = _run_batch(scenes, iters, _params(mapping=mapping), cfs)
+    for p, sc in enumerate(scenes):
+        est = ppm.Estimator(hps[p], sc.r0, params=_params(mapping=mapping, cell_factor=cfs[p]))
+        for i in range(iters):
+            est.step(phs[i][p])
+            one = {k: v.cpu().numpy() for k, v in est.state().items()}
+            for k in one:
+                assert np.array_equal(one[k], states[i][p][k]), (p, i, k)
+            assert est.stats().pairs == stats[i][p].pairs
+        assert np.array_equal(est.radiance().cpu().numpy(), L[p])
+        est.close()
+
+
+def test_batch_rejects_bad_iterations():
+    from paper_2504_04411_gb300 import ppm
+    scenes = _problems()[:2]
+    hps = [s.hitpoints("cuda") for s in scenes]
+    b = ppm.Batch(hps, [s.r0 for s in scenes], [s.J for s in scenes])
+    good = [s.photons(1, "cuda") for s in scenes]
+    short = synth.Photons(good[0].pos[:-1].contiguous(), good[0].flux[:-1].contiguous(),
+                          good[0].nq[:-1].contiguous(), None, None)
+    with pytest.raises(ppm.PPMError) as e:
+        ppm.ppm_batch_iterate(b.b, [short, good[1]], 1)
+    assert e.value.code == ppm.PPM_EINVAL
+    with pytest.raises(ppm.PPMError) as e:
+        ppm.ppm_batch_iterate(b.b, good, 2)
+    assert e.value.code == ppm.PPM_ESTATE
+    b.step(good)
+    assert b.stats()[0].iter == 1
+    b.close()
