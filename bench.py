@@ -164,7 +164,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="frame", choices=["frame", "tiny", "batched"])
+    ap.add_argument("--config", default="frame", choices=["frame", "tiny", "batched", "learned"])
     ap.add_argument("--mapping", type=int, default=None, help="skip the autotuner: traversal")
     ap.add_argument("--cell-factor", type=float, default=None, help="skip the autotuner: cell factor")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -172,7 +172,7 @@ def parse():
     ap.add_argument("--no-flush", action="store_true")
     a = ap.parse_args()
     if a.steps is None:
-        a.steps = 16 if a.config == "batched" else 64 - a.warmup
+        a.steps = 16 if a.config == "batched" else (64 if a.config == "learned" else 64 - a.warmup)
     return a
 
 
@@ -232,6 +232,8 @@ def main():
     __graft_entry__.build()
     if args.config == "batched":
         line = run_batched(args, rank, world, local, dist)
+    elif args.config == "learned":
+        line = run_learned(args, rank, world, local, dist)
     else:
         line = run_single(args, rank, world, local, dist)
     if rank == 0:
@@ -456,6 +458,66 @@ def run_batched(args, rank, world, local, dist):
             "vs_plain": {"value": plain_pairs / plain_s, "unit": UNIT,
                          "speedup": value / (plain_pairs / plain_s),
                          "equal_mse": "bit-identical state and radiance per problem (tested)"}}
+
+
+def run_learned(args, rank, world, local, dist):
+    """Learned radius proposer vs the plain method on the tiny configuration
+    at equal radiance MSE: the network is trained (own kernels) on 200 plain
+    iterations of one seed, both methods then run on a fresh seed; the
+    metric is the learned run's pair-test rate, with the iterations and
+    device time each needs to reach the plain method's final MSE."""
+    import torch
+
+    from paper_2504_04411_gb300 import learned, ppm, synth
+    N = args.steps if args.steps else 64
+    train_sc = synth.PlaneScene(nside=64, J=100_000, r0=0.02, step=True, seed=synth.SEED_BASE + 500 + 1000 * rank)
+    t0 = time.perf_counter()
+    tr = learned.run(train_sc, 200)
+    X, Y, M = learned.dataset(tr)
+    blob, _, losses = learned.train(X, Y, M, epochs=20)
+    train_s = time.perf_counter() - t0
+    test_sc = synth.PlaneScene(nside=64, J=100_000, r0=0.02, step=True, seed=synth.SEED_BASE + 600 + 1000 * rank)
+    hp = test_sc.hitpoints("cuda")
+    ref = (hp.pos[:, 0] < 0.5).float()
+    batches = [test_sc.photons(i, "cuda") for i in range(1, N + 1)]
+
+    def timed(blob_):
+        est = ppm.Estimator(hp, test_sc.r0, 0.75)
+        if blob_ is not None:
+            ppm.ppm_set_mlp(est.ctx, blob_, 0.5, 0.1)
+        ms, mse, pairs = [], [], 0
+        stream = torch.cuda.current_stream()
+        for ph in batches:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            est.step(ph)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+            mse.append(float(((est.radiance() - ref) ** 2).mean()))
+            pairs += est.stats().pairs
+        est.close()
+        return ms, mse, pairs
+
+    pms, pmse, ppairs = timed(None)
+    lms, lmse, lpairs = timed(blob)
+    target = pmse[-1]
+    reach = learned.iterations_to_reach(lmse, target)
+    t_plain = sum(pms)
+    t_learn = sum(lms[:reach]) if reach else None
+    return {"metric": METRIC, "value": lpairs / (sum(lms) / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": N, "warmup": 0, "ms_per_step": sum(lms) / N, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (BF16 network weights)", "data": "synthetic",
+            "config": {"workload": "learned radius: tiny config (64x64 hit points, 100k photons/iter, "
+                                   "step edge, r0=0.02), MLP 12-64-64-2 trained on 200 plain iterations",
+                       "hit_points": 4096, "photons_per_iter": 100_000, "l2": "not flushed (small)",
+                       "parallelism": "single GPU"},
+            "equal_mse": {"target_mse": target, "plain_iterations": N, "learned_iterations": reach,
+                          "plain_ms": t_plain, "learned_ms": t_learn,
+                          "speedup": (t_plain / t_learn) if t_learn else None,
+                          "mse_at_16": {"plain": pmse[15], "learned": lmse[15]} if N >= 16 else None},
+            "training": {"samples": int(X.shape[0]), "epochs": 20, "final_loss": losses[-1],
+                         "seconds": train_s}}
 
 
 def run_reference(args):

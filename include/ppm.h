@@ -122,6 +122,7 @@ typedef struct {
     int32_t launches;      /* kernels launched by the last build + gather */
     float gather_ms;       /* batches: device time of the last gather launch
                               (events recorded around it); contexts: -1 */
+    int64_t proposals;     /* radii shrunk by the learned proposer */
 } ppm_iter_stats;
 
 /* State per hit point, in the caller's hit-point order (device pointers;
@@ -198,6 +199,51 @@ int ppm_f_critical(int64_t J, double alpha_f, int32_t t_max, double* out, void* 
  * scratch cannot be allocated. */
 int ppm_sort_pairs(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
                    uint32_t* vals_out, int64_t n, int32_t bits, void* stream);
+
+/* ---- learned radius proposer (not in the paper) ----------------------------
+ * A 12 -> 64 -> 64 -> 2 MLP with ReLU hidden layers, BF16 weights, FP32
+ * biases, activations and accumulation.  Input: 12 features of the window a
+ * hit point's F-test just used -- log(1+C), log(1+t'), log i, r/r0,
+ * log(r/r0), log(1+F), F/F_c, max_g S_g/S, min_g S_g/S, fraction of empty
+ * groups, coefficient of variation of the group sums, max_g c_g/C (C, S:
+ * window count and psi sum; channel 0).  Outputs: o0 = predicted
+ * log(r_final / r), o1 = logit of "will be rejected within a few tests".
+ * Weight blob (device, 16-byte aligned, PPM_MLP_BLOB_BYTES): W1 [64][12],
+ * W2 [64][64], W3 [2][64] as bf16 row-major, then b1[64], b2[64], b3[2] as
+ * float.  Master parameters (FP32, PPM_MLP_PARAMS floats): the same order. */
+#define PPM_MLP_IN 12
+#define PPM_MLP_HIDDEN 64
+#define PPM_MLP_OUT 2
+#define PPM_MLP_PARAMS (64 * 12 + 64 * 64 + 2 * 64 + 64 + 64 + 2)
+#define PPM_MLP_BLOB_BYTES 10504
+
+/* Allocate (enable != 0) or free the per-hit-point feature buffer; while it
+ * exists every ppm_gather_test_update writes the features of its tests. */
+int ppm_set_features(ppm_ctx* ctx, int32_t enable);
+/* Features of the last iteration's tests into out (device, n x 12,
+ * caller's hit-point order); PPM_ESTATE if features are not enabled. */
+int ppm_get_features(ppm_ctx* ctx, float* out);
+/* Enable (blob != NULL) or disable the proposer.  After the F-test update
+ * of each iteration, a hit point the test did not reject gets
+ * r <- max(r max(exp(o0), min_ratio), bound of Eq. radiusupdate) when
+ * sigmoid(o1) > doom_threshold and o0 < 0, and its window is cleared; the
+ * F-test keeps testing every radius.  The blob is borrowed (caller-owned)
+ * until the proposer is disabled or the context destroyed. */
+int ppm_set_mlp(ppm_ctx* ctx, const void* blob, float doom_threshold, float min_ratio);
+/* Inference: X n x 12 float, Y n x 2 float (device). */
+int ppm_mlp_forward(const void* blob, const float* X, int64_t n, float* Y, void* stream);
+/* Gradient of scale * sum_s [0.5 M0 (o0 - Y0)^2 + M1 BCE(o1, Y1)] over the
+ * n samples (X n x 12, Y and M n x 2) with respect to the master
+ * parameters, ADDED to grad (PPM_MLP_PARAMS floats); the loss is added to
+ * *loss.  Forward passes use the blob's BF16 weights. */
+int ppm_mlp_grad(const void* blob, const float* X, const float* Y, const float* M, int64_t n,
+                 float scale, float* grad, float* loss, void* stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, step >= 1) on master with
+ * moments m, v; rewrites the blob from the new master and zeroes grad. */
+int ppm_mlp_adam(float* master, float* grad, float* m, float* v, int32_t step, float lr,
+                 void* blob, void* stream);
+/* Blob from master (BF16 round to nearest even). */
+int ppm_mlp_pack(const float* master, void* blob, void* stream);
 
 /* ---- batches: many independent problems per launch --------------------
  * A batch holds n_problems independent problem instances (hit points,

@@ -1,0 +1,77 @@
+"""FP64 reference of the learned radius proposer's network and of its loss
+gradient (numpy).
+
+TEST INFRASTRUCTURE ONLY (imported by tests/), independent of the CUDA
+sources.  The network is 12 -> 64 -> 64 -> 2 with ReLU hidden layers; the
+weights given to the GPU are BF16, so the reference decodes the same BF16
+bits (exactly representable in FP64) and evaluates everything in FP64.
+Loss per sample: 0.5 m0 (o0 - y0)^2 + m1 BCE(o1, y1), BCE(z, y) =
+max(z, 0) - z y + log(1 + exp(-|z|)), times a common scale.
+Pinned in tests/test_mlp_oracle.py by central finite differences.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+N_IN, N_H, N_OUT = 12, 64, 2
+SHAPES = [("W1", (N_H, N_IN)), ("W2", (N_H, N_H)), ("W3", (N_OUT, N_H)),
+          ("b1", (N_H,)), ("b2", (N_H,)), ("b3", (N_OUT,))]
+N_PARAMS = sum(int(np.prod(s)) for _, s in SHAPES)
+N_WEIGHTS = N_H * N_IN + N_H * N_H + N_OUT * N_H
+BLOB_BYTES = 2 * N_WEIGHTS + 4 * (N_H + N_H + N_OUT)
+
+
+def split(flat: np.ndarray) -> dict:
+    out, o = {}, 0
+    for name, shape in SHAPES:
+        k = int(np.prod(shape))
+        out[name] = np.asarray(flat[o:o + k], np.float64).reshape(shape)
+        o += k
+    return out
+
+
+def from_blob(blob: bytes | np.ndarray) -> dict:
+    """Decode the device blob layout (bf16 W1, W2, W3; f32 b1, b2, b3)."""
+    raw = np.frombuffer(bytes(blob), dtype=np.uint8)
+    w16 = raw[:2 * N_WEIGHTS].view(np.uint16).astype(np.uint32) << 16
+    weights = w16.view(np.float32).astype(np.float64)
+    biases = raw[2 * N_WEIGHTS:BLOB_BYTES].view(np.float32).astype(np.float64)
+    return split(np.concatenate([weights, biases]))
+
+
+def forward(p: dict, X: np.ndarray):
+    X = np.asarray(X, np.float64)
+    z1 = X @ p["W1"].T + p["b1"]
+    h1 = np.maximum(z1, 0.0)
+    z2 = h1 @ p["W2"].T + p["b2"]
+    h2 = np.maximum(z2, 0.0)
+    out = h2 @ p["W3"].T + p["b3"]
+    return out, (X, z1, h1, z2, h2)
+
+
+def loss_and_grad(p: dict, X, Y, M, scale: float):
+    """Loss and its gradient w.r.t. every parameter, flattened in the order
+    W1, W2, W3, b1, b2, b3 (the master-parameter order)."""
+    out, (X, z1, h1, z2, h2) = forward(p, X)
+    Y = np.asarray(Y, np.float64)
+    M = np.asarray(M, np.float64)
+    e = out[:, 0] - Y[:, 0]
+    z = out[:, 1]
+    bce = np.maximum(z, 0) - z * Y[:, 1] + np.log1p(np.exp(-np.abs(z)))
+    loss = scale * np.sum(0.5 * M[:, 0] * e * e + M[:, 1] * bce)
+    sig = 1.0 / (1.0 + np.exp(-z))
+    dout = scale * np.stack([M[:, 0] * e, M[:, 1] * (sig - Y[:, 1])], 1)
+    dW3 = dout.T @ h2
+    db3 = dout.sum(0)
+    dh2 = (dout @ p["W3"]) * (z2 > 0)
+    dW2 = dh2.T @ h1
+    db2 = dh2.sum(0)
+    dh1 = (dh2 @ p["W2"]) * (z1 > 0)
+    dW1 = dh1.T @ X
+    db1 = dh1.sum(0)
+    grad = np.concatenate([dW1.ravel(), dW2.ravel(), dW3.ravel(), db1, db2, db3])
+    return loss, grad
+
+
+def loss_only(flat: np.ndarray, X, Y, M, scale: float) -> float:
+    return loss_and_grad(split(flat), X, Y, M, scale)[0]

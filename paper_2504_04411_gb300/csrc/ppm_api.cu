@@ -210,7 +210,7 @@ void free_ctx(ppm_ctx* c)
     cudaFree(c->pack0); cudaFree(c->pack1); cudaFree(c->pack_aux);
     ppm_sort_scratch_free(&c->sort);
     cudaFree(c->geom_dev); cudaFree(c->rmax); cudaFree(c->fc);
-    cudaFree(c->counters); cudaFree(c->err_dev);
+    cudaFree(c->counters); cudaFree(c->err_dev); cudaFree(c->feat);
     delete c;
 }
 
@@ -319,7 +319,7 @@ int ppm_create(const ppm_hitpoints* hp, float r0, float alpha, const ppm_params*
               dalloc(&c->hp_v, n) && dalloc(&c->r, n) && dalloc(&c->t, n) && dalloc(&c->F, n) &&
               dalloc(&c->tau, n * c->nch) && dalloc(&c->cnt, n * PPM_NG) &&
               dalloc(&c->S, n * PPM_NG * c->ntc) && dalloc(&c->Q, n * PPM_NG * c->ntc) &&
-              dalloc(&c->geom_dev, 1) && dalloc(&c->rmax, 2) && dalloc(&c->counters, 4) &&
+              dalloc(&c->geom_dev, 1) && dalloc(&c->rmax, 2) && dalloc(&c->counters, 8) &&
               dalloc(&c->err_dev, 1);
     if (!ok) { free_ctx(c); return PPM_ENOMEM; }
     cudaStream_t st = c->stream;
@@ -337,7 +337,7 @@ int ppm_create(const ppm_hitpoints* hp, float r0, float alpha, const ppm_params*
             cudaMemsetAsync(c->cnt, 0, n * PPM_NG * sizeof(uint32_t), st) != cudaSuccess ||
             cudaMemsetAsync(c->S, 0, n * PPM_NG * c->ntc * sizeof(float), st) != cudaSuccess ||
             cudaMemsetAsync(c->Q, 0, n * PPM_NG * c->ntc * sizeof(float), st) != cudaSuccess ||
-            cudaMemsetAsync(c->counters, 0, 4 * sizeof(unsigned long long), st) != cudaSuccess ||
+            cudaMemsetAsync(c->counters, 0, 8 * sizeof(unsigned long long), st) != cudaSuccess ||
             cudaMemsetAsync(c->err_dev, 0, sizeof(int32_t), st) != cudaSuccess) { rc = PPM_ECUDA; break; }
         float rm[2] = {r0, 0.f};
         if (cudaMemcpyAsync(c->rmax, rm, sizeof(rm), cudaMemcpyHostToDevice, st) != cudaSuccess ||
@@ -385,8 +385,14 @@ int ppm_gather_test_update(ppm_ctx* c, int32_t iter)
     const float bound = (float)((double)c->r_min * sqrt(pow((double)iter + 1.0, (double)c->alpha - 1.0)));
     PPM_CUDA(cudaMemsetAsync(c->rmax + (c->rmax_cur ^ 1), 0, sizeof(float), c->stream));
     PPM_CUDA(cudaMemsetAsync(c->counters, 0, 3 * sizeof(unsigned long long), c->stream));
+    PPM_CUDA(cudaMemsetAsync(c->counters + 4, 0, sizeof(unsigned long long), c->stream));
     rc = ppm_gather_launch(c, bound);
     if (rc) return rc;
+    if (c->mlp) {
+        rc = ppm_mlp_propose_launch(c, bound);
+        if (rc) return rc;
+        ++launches;
+    }
     c->iter = iter;
     c->rmax_cur ^= 1;
     c->grid_valid = false;
@@ -445,7 +451,7 @@ int ppm_stats(ppm_ctx* c, ppm_iter_stats* out)
 {
     PPM_ENTRY();
     if (!c || !out) return PPM_EINVAL;
-    unsigned long long cnt[4];
+    unsigned long long cnt[5];
     float rm;
     GridGeom g;
     int32_t err;
@@ -465,6 +471,7 @@ int ppm_stats(ppm_ctx* c, ppm_iter_stats* out)
     out->cell = g.h;
     out->launches = c->launches_iter;
     out->gather_ms = -1.f;
+    out->proposals = (int64_t)cnt[4];
     return PPM_OK;
 }
 

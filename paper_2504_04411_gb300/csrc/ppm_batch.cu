@@ -260,6 +260,8 @@ k_batch_gather(GatherArgs a, BatchArgs bt)
         pr.n_vm = bt.nvm[p];
         pr.fc_max = kFcCap;
         pr.pid = (uint32_t)p;
+        pr.inv_r0 = 0.f;
+        pr.log_iter = 0.f;
         gather_block<NCH, NTC, NORMALS, VCM, MAPPING, true>(a, pr, T.y, T.z, sm, &us_raw);
     }
 }
@@ -349,6 +351,7 @@ int run_gather(ppm_batch* b)
     a.cell_start = b->cell_start;
     a.rec0 = b->rec0; a.rec1 = b->rec1; a.aux = b->aux;
     a.err = b->err;
+    a.feat = nullptr;
     BatchArgs bt;
     bt.tiles = b->tiles; bt.ntiles = b->ntiles; bt.head = b->head;
     bt.geom = b->geom; bt.fc = b->fc; bt.rmax_next = b->rmax_next; bt.counters = b->counters;

@@ -74,6 +74,7 @@ int ppm_gather_launch(ppm_ctx* c, float bound)
     a.cell_start = c->cell_start;
     a.rec0 = c->rec0; a.rec1 = c->rec1; a.aux = c->aux;
     a.err = c->err_dev;
+    a.feat = c->feat;
     Prob pr;
     pr.geom = c->geom_dev;
     pr.fc = c->fc;
@@ -85,6 +86,8 @@ int ppm_gather_launch(ppm_ctx* c, float bound)
     pr.n_vm = c->prm.n_vm > 0.f ? c->prm.n_vm : (float)c->J;
     pr.fc_max = c->fc_upto;
     pr.pid = 0u;
+    pr.inv_r0 = 1.0f / c->r0;
+    pr.log_iter = logf((float)(c->iter + 1));
     const bool nrm = c->use_normals;
     const bool vcm = c->prm.vcm != 0;
     if (c->nch == 1) {

@@ -29,6 +29,7 @@ struct GatherArgs {
     uint32_t* cnt;
     float* S;
     float* Q;
+    float* feat;        // [12][nh] features of the learned proposer, or NULL
     const uint32_t* cell_start;
     const float4* rec0;
     const float4* rec1;
@@ -45,7 +46,15 @@ struct Prob {
     float J, k, bound, n_vm;
     int32_t fc_max;                 // last valid index of fc
     uint32_t pid;                   // problem id carried by its photons (batch)
+    float inv_r0;                   // features: 1 / initial radius
+    float log_iter;                 // features: log of the iteration index
 };
+
+// The 12 features of the learned radius proposer, from the window the test
+// just used (channel 0): log(1+C), log(1+t'), log i, r/r0, log(r/r0),
+// log(1+F), F/F_c, max_g S_g/S, min_g S_g/S, fraction of empty groups,
+// coefficient of variation of the group sums, max_g c_g/C.
+constexpr int kFeatures = 12;
 
 template <int NTC>
 struct Smem {
@@ -399,6 +408,29 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
             if (ssw > 0.f) F = (dev2 / ssw) * (((float)PPM_NG * (m - 1.0f)) / ((float)(PPM_NG - 1) * m));
             if (c == 0) F0 = F;
             if (ssw > 0.f && (double)F > pr.fc[tpi]) reject = true;
+            if (c == 0 && a.feat) {
+                uint32_t C = 0, cmax = 0, empty = 0;
+                float smax = 0.f, smin = Sg[0];
+#pragma unroll
+                for (int g = 0; g < PPM_NG; ++g) {
+                    const uint32_t cg = a.cnt[g * nh + h] + sm.c[g][tid];
+                    C += cg;
+                    cmax = max(cmax, cg);
+                    empty += cg == 0u;
+                    smax = fmaxf(smax, Sg[g]);
+                    smin = fminf(smin, Sg[g]);
+                }
+                const float fc = (float)pr.fc[tpi];
+                const float f[kFeatures] = {
+                    log1pf((float)C), log1pf((float)tp), pr.log_iter, r * pr.inv_r0,
+                    logf(fmaxf(r * pr.inv_r0, 1e-30f)), log1pf(F), F / fc,
+                    Ssum > 0.f ? smax / Ssum : 0.f, Ssum > 0.f ? smin / Ssum : 0.f,
+                    (float)empty * (1.0f / PPM_NG),
+                    Ssum > 0.f ? sqrtf(dev2 * (1.0f / PPM_NG)) / (Ssum * (1.0f / PPM_NG)) : 0.f,
+                    C > 0u ? (float)cmax / (float)C : 0.f};
+#pragma unroll
+                for (int q = 0; q < kFeatures; ++q) a.feat[(int64_t)q * nh + h] = f[q];
+            }
         }
         // Eq. (progressive-VCM-estimator): kernel estimate with this r_i;
         // Phi_i = sum over groups of this iteration's psi sums unless RGB

@@ -173,6 +173,11 @@ struct ppm_ctx {
     int32_t iter = 0;
     int32_t launches_build = 0;       // kernels launched by the last build
     int32_t launches_iter = 0;        // ... by the last build + gather
+    // learned radius proposer (ppm_mlp.cu)
+    float* feat = nullptr;            // [12][nh] features of the last test
+    const void* mlp = nullptr;        // caller-owned weight blob (device) or NULL
+    float mlp_threshold = 0.5f;
+    float mlp_max_shrink = 0.1f;
 };
 
 // ppm_grid.cu / ppm_gather.cu
@@ -191,3 +196,5 @@ int ppm_prepare_hitpoints(const ppm_hitpoints* hp, bool with_rho, uint32_t* orig
                           float4* u, float4* v, cudaStream_t st);
 int ppm_gather_launch(ppm_ctx* c, float bound);
 int ppm_radiance_launch(ppm_ctx* c, float* out);
+// learned proposer after the F-test update of iteration c->iter
+int ppm_mlp_propose_launch(ppm_ctx* c, float bound);

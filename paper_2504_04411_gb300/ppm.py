@@ -46,7 +46,8 @@ class ppm_iter_stats(ctypes.Structure):
                 ("pairs", ctypes.c_int64), ("candidates", ctypes.c_int64),
                 ("rejects", ctypes.c_int64), ("pairs_total", ctypes.c_int64),
                 ("r_max", ctypes.c_float), ("cell", ctypes.c_float),
-                ("launches", ctypes.c_int32), ("gather_ms", ctypes.c_float)]
+                ("launches", ctypes.c_int32), ("gather_ms", ctypes.c_float),
+                ("proposals", ctypes.c_int64)]
 
 
 class ppm_state_view(ctypes.Structure):
@@ -61,7 +62,8 @@ EXPORTS = ("ppm_default_params", "ppm_create", "ppm_set_stream", "ppm_build_grid
            "ppm_destroy", "ppm_strerror", "ppm_sort_pairs_noalloc",
            "ppm_batch_create", "ppm_batch_iterate", "ppm_batch_radiance",
            "ppm_batch_get_state", "ppm_batch_stats", "ppm_batch_graph_ready",
-           "ppm_batch_destroy")
+           "ppm_batch_destroy", "ppm_set_features", "ppm_get_features", "ppm_set_mlp",
+           "ppm_mlp_forward", "ppm_mlp_grad", "ppm_mlp_adam", "ppm_mlp_pack")
 
 _lib = None
 
@@ -117,6 +119,20 @@ def load(path: str = LIB_PATH):
     L.ppm_batch_graph_ready.argtypes = [c_p]
     L.ppm_batch_destroy.restype = None
     L.ppm_batch_destroy.argtypes = [c_p]
+    L.ppm_set_features.restype = ctypes.c_int
+    L.ppm_set_features.argtypes = [c_p, ctypes.c_int32]
+    L.ppm_get_features.restype = ctypes.c_int
+    L.ppm_get_features.argtypes = [c_p, c_p]
+    L.ppm_set_mlp.restype = ctypes.c_int
+    L.ppm_set_mlp.argtypes = [c_p, c_p, ctypes.c_float, ctypes.c_float]
+    L.ppm_mlp_forward.restype = ctypes.c_int
+    L.ppm_mlp_forward.argtypes = [c_p, c_p, ctypes.c_int64, c_p, c_p]
+    L.ppm_mlp_grad.restype = ctypes.c_int
+    L.ppm_mlp_grad.argtypes = [c_p, c_p, c_p, c_p, ctypes.c_int64, ctypes.c_float, c_p, c_p, c_p]
+    L.ppm_mlp_adam.restype = ctypes.c_int
+    L.ppm_mlp_adam.argtypes = [c_p, c_p, c_p, c_p, ctypes.c_int32, ctypes.c_float, c_p, c_p]
+    L.ppm_mlp_pack.restype = ctypes.c_int
+    L.ppm_mlp_pack.argtypes = [c_p, c_p, c_p]
     L.ppm_destroy.restype = None
     L.ppm_destroy.argtypes = [c_p]
     L.ppm_strerror.restype = ctypes.c_char_p
@@ -232,6 +248,42 @@ def ppm_sort_pairs_noalloc(keys_in, vals_in, keys_out, vals_out, bits: int, stre
     _check("ppm_sort_pairs_noalloc",
            load().ppm_sort_pairs_noalloc(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out),
                                          _ptr(vals_out), keys_in.numel(), bits, _stream(stream)))
+
+
+PPM_MLP_IN, PPM_MLP_HIDDEN, PPM_MLP_OUT = 12, 64, 2
+PPM_MLP_PARAMS = 64 * 12 + 64 * 64 + 2 * 64 + 64 + 64 + 2
+PPM_MLP_BLOB_BYTES = 10504
+
+
+def ppm_set_features(ctx, enable: bool = True) -> None:
+    _check("ppm_set_features", load().ppm_set_features(ctx, int(enable)))
+
+
+def ppm_get_features(ctx, out) -> None:
+    _check("ppm_get_features", load().ppm_get_features(ctx, _ptr(out)))
+
+
+def ppm_set_mlp(ctx, blob, doom_threshold: float = 0.5, min_ratio: float = 0.1) -> None:
+    _check("ppm_set_mlp", load().ppm_set_mlp(ctx, _ptr(blob), doom_threshold, min_ratio))
+
+
+def ppm_mlp_forward(blob, X, Y, stream=None) -> None:
+    _check("ppm_mlp_forward", load().ppm_mlp_forward(_ptr(blob), _ptr(X), X.shape[0], _ptr(Y),
+                                                     _stream(stream)))
+
+
+def ppm_mlp_grad(blob, X, Y, M, scale: float, grad, loss, stream=None) -> None:
+    _check("ppm_mlp_grad", load().ppm_mlp_grad(_ptr(blob), _ptr(X), _ptr(Y), _ptr(M), X.shape[0],
+                                               scale, _ptr(grad), _ptr(loss), _stream(stream)))
+
+
+def ppm_mlp_adam(master, grad, m, v, step: int, lr: float, blob, stream=None) -> None:
+    _check("ppm_mlp_adam", load().ppm_mlp_adam(_ptr(master), _ptr(grad), _ptr(m), _ptr(v), step, lr,
+                                               _ptr(blob), _stream(stream)))
+
+
+def ppm_mlp_pack(master, blob, stream=None) -> None:
+    _check("ppm_mlp_pack", load().ppm_mlp_pack(_ptr(master), _ptr(blob), _stream(stream)))
 
 
 def ppm_destroy(ctx) -> None:

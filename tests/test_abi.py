@@ -46,5 +46,5 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(ppm.ppm_hitpoints) == 48
     assert ctypes.sizeof(ppm.ppm_photons) == 64
     assert ctypes.sizeof(ppm.ppm_params) == 64
-    assert ctypes.sizeof(ppm.ppm_iter_stats) == 56
+    assert ctypes.sizeof(ppm.ppm_iter_stats) == 64
     assert ctypes.sizeof(ppm.ppm_state_view) == 56

@@ -1,0 +1,216 @@
+"""The learned radius proposer's kernels through the C ABI against the FP64
+network oracle (forward, loss, gradient), the BF16 packing, training, the
+window features against values derived from the method oracle, and the
+proposer switched off reproducing the plain method bit for bit."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as MO
+from oracle import oracle as O
+from paper_2504_04411_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _bf16_rne(x: np.ndarray) -> np.ndarray:
+    """float32 -> bf16 bits, round to nearest even (no NaNs here)."""
+    u = x.astype(np.float32).view(np.uint32).astype(np.uint64)
+    u = u + 0x7FFF + ((u >> 16) & 1)
+    return (u >> 16).astype(np.uint16)
+
+
+def _host_blob(master: np.ndarray) -> bytes:
+    return _bf16_rne(master[:MO.N_WEIGHTS]).tobytes() + master[MO.N_WEIGHTS:].astype(np.float32).tobytes()
+
+
+def _to_dev_blob(blob: bytes):
+    import torch
+    buf = np.zeros(MO.BLOB_BYTES // 4 + 4, np.int32)
+    buf.view(np.uint8)[:MO.BLOB_BYTES] = np.frombuffer(blob, np.uint8)
+    return torch.from_numpy(buf).cuda()
+
+
+def _random_net(seed, n=1500):
+    rng = np.random.default_rng(seed)
+    master = np.concatenate([rng.normal(0, math.sqrt(2 / 12), 768), rng.normal(0, math.sqrt(2 / 64), 4096),
+                             rng.normal(0, math.sqrt(2 / 64), 128), rng.normal(0, 0.1, 130)]).astype(np.float32)
+    X = rng.normal(0, 1, (n, 12)).astype(np.float32)
+    Y = np.stack([rng.normal(-1, 1, n), rng.integers(0, 2, n)], 1).astype(np.float32)
+    M = rng.uniform(0, 1, (n, 2)).astype(np.float32)
+    return master, X, Y, M
+
+
+def test_forward_matches_oracle():
+    import torch
+    from paper_2504_04411_gb300 import ppm
+    master, X, _, _ = _random_net(1)
+    blob = _host_blob(master)
+    out = torch.empty(X.shape[0], 2, device="cuda")
+    ppm.ppm_mlp_forward(_to_dev_blob(blob), torch.from_numpy(X).cuda(), out)
+    ref, _ = MO.forward(MO.from_blob(blob), X)
+    got = out.cpu().numpy().astype(np.float64)
+    assert np.allclose(got, ref, rtol=1e-4, atol=1e-4 * np.abs(ref).max())
+
+
+def test_gradient_matches_oracle():
+    import torch
+    from paper_2504_04411_gb300 import ppm
+    master, X, Y, M = _random_net(2, n=2000)
+    blob = _host_blob(master)
+    grad = torch.zeros(MO.N_PARAMS, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    scale = 1.0 / X.shape[0]
+    ppm.ppm_mlp_grad(_to_dev_blob(blob), torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(),
+                     torch.from_numpy(M).cuda(), scale, grad, loss)
+    ref_loss, ref = MO.loss_and_grad(MO.from_blob(blob), X, Y, M, scale)
+    g = grad.cpu().numpy().astype(np.float64)
+    assert float(loss) == pytest.approx(ref_loss, rel=1e-5)
+    err = np.abs(g - ref)
+    assert np.all(err <= 1e-3 * np.abs(ref) + 1e-5 * np.abs(ref).max()), float((err / (np.abs(ref) + 1e-12)).max())
+
+
+def test_pack_rounds_to_nearest_even():
+    import torch
+    from paper_2504_04411_gb300 import ppm
+    master, _, _, _ = _random_net(3)
+    dev = torch.zeros(MO.BLOB_BYTES // 4 + 4, dtype=torch.int32, device="cuda")
+    ppm.ppm_mlp_pack(torch.from_numpy(master).cuda(), dev)
+    got = dev.cpu().numpy().view(np.uint8)[:MO.BLOB_BYTES].tobytes()
+    assert got == _host_blob(master)
+
+
+def test_training_reduces_loss():
+    import torch
+    from paper_2504_04411_gb300 import learned
+    rng = np.random.default_rng(4)
+    X = rng.normal(0, 1, (20000, 12)).astype(np.float32)
+    w = rng.normal(0, 1, 12)
+    y0 = np.tanh(X @ w / 4) - 1
+    y1 = (X[:, 0] + X[:, 3] > 0).astype(np.float32)
+    Y = torch.from_numpy(np.stack([y0, y1], 1).astype(np.float32)).cuda()
+    blob, master, losses = learned.train(torch.from_numpy(X).cuda(), Y, torch.ones_like(Y), epochs=12)
+    assert losses[-1] < 0.35 * losses[0], losses
+    assert all(b <= a * 1.05 for a, b in zip(losses, losses[1:])), losses
+
+
+def _derived_features(ref, it, r0, i):
+    """FP64 features of iteration it from the oracle's window statistics."""
+    C = ref.counts[it].sum(1).astype(np.float64)
+    S = ref.S[it]
+    Ssum = S.sum(1)
+    # window length: iterations since the last rejection, plus this one
+    tp = np.ones(C.shape[0])
+    for k in range(it):
+        tp = np.where(ref.reject[k], 1.0, tp + 1.0)
+    r = ref.r[it].astype(np.float64)
+    F, Fc = ref.F[it], ref.Fc[it]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        cv = np.where(Ssum > 0, np.sqrt(((S - Ssum[:, None] / 12) ** 2).sum(1) / 12) / (Ssum / 12), 0)
+        f = np.stack([np.log1p(C), np.log1p(tp), np.full_like(C, math.log(i)), r / r0, np.log(r / r0),
+                      np.log1p(F), F / Fc, np.where(Ssum > 0, S.max(1) / Ssum, 0),
+                      np.where(Ssum > 0, S.min(1) / Ssum, 0), (ref.counts[it] == 0).sum(1) / 12, cv,
+                      np.where(C > 0, ref.counts[it].max(1) / C, 0)], 1)
+    return f
+
+
+def test_features_match_oracle():
+    import torch
+    from paper_2504_04411_gb300 import ppm
+    sc = synth.PlaneScene(nside=32, J=30_000, r0=0.04, step=True, seed=synth.SEED_BASE + 40)
+    hp = sc.hitpoints("cuda")
+    iters = 3
+    batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
+    est = ppm.Estimator(hp, sc.r0)
+    ppm.ppm_set_features(est.ctx, True)
+    feats = []
+    out = torch.empty(hp.n, 12, device="cuda")
+    for ph in batches:
+        est.step(ph)
+        ppm.ppm_get_features(est.ctx, out)
+        feats.append(out.cpu().numpy().astype(np.float64))
+    est.close()
+    ref = O.run(hp.numpy(), synth.stack_numpy(batches), sc.r0, iters)
+    alive = np.ones(hp.n, bool)
+    for it in range(iters):
+        want = _derived_features(ref, it, sc.r0, it + 1)
+        got = feats[it]
+        # F-dependent features carry the FP32 statistics' rounding
+        tol = np.array([1e-5, 1e-6, 1e-6, 1e-6, 1e-5, 1e-3, 1e-3, 1e-4, 1e-4, 0, 1e-3, 1e-6])
+        err = np.abs(got - want)[alive]
+        assert np.all(err <= tol * np.maximum(np.abs(want[alive]), 1) + 1e-6), (it, err.max(0))
+
+
+def test_features_and_disabled_proposer_leave_the_method_unchanged():
+    import torch
+    from paper_2504_04411_gb300 import ppm
+    sc = synth.PlaneScene(nside=24, J=20_000, r0=0.04, step=True, seed=synth.SEED_BASE + 41)
+    hp = sc.hitpoints("cuda")
+    batches = [sc.photons(i, "cuda") for i in range(1, 6)]
+    finals = []
+    for mode in ("plain", "features", "disabled"):
+        est = ppm.Estimator(hp, sc.r0)
+        if mode != "plain":
+            ppm.ppm_set_features(est.ctx, True)
+        if mode == "disabled":
+            blob = torch.zeros(ppm.PPM_MLP_BLOB_BYTES // 4 + 4, dtype=torch.int32, device="cuda")
+            ppm.ppm_set_mlp(est.ctx, blob)
+            ppm.ppm_set_mlp(est.ctx, None)
+        for ph in batches:
+            est.step(ph)
+        finals.append({k: v.cpu() for k, v in est.state().items()})
+        est.close()
+    for k in finals[0]:
+        assert torch.equal(finals[0][k], finals[1][k]) and torch.equal(finals[0][k], finals[2][k]), k
+
+
+def test_proposer_only_shrinks_and_respects_the_bound():
+    import torch
+    from paper_2504_04411_gb300 import ppm
+    sc = synth.PlaneScene(nside=32, J=30_000, r0=0.04, step=True, seed=synth.SEED_BASE + 42)
+    hp = sc.hitpoints("cuda")
+    # a network that calls everything doomed and asks for half the radius:
+    # all weights zero, b3 = (log 0.5, +10)
+    master = np.zeros(MO.N_PARAMS, np.float32)
+    master[-2:] = [math.log(0.5), 10.0]
+    blob = _to_dev_blob(_host_blob(master))
+    est = ppm.Estimator(hp, sc.r0)
+    ppm.ppm_set_mlp(est.ctx, blob, 0.5, 0.1)
+    prev = torch.full((hp.n,), sc.r0, device="cuda")
+    for i in range(1, 5):
+        est.step(sc.photons(i, "cuda"))
+        st = est.state()
+        assert torch.all(st["r"] <= prev)
+        bound = O.radius_bound(1e-3 * sc.r0, 0.75, i)
+        assert torch.all(st["r"] >= bound * (1 - 1e-6))
+        assert est.stats().proposals > 0
+        assert torch.all(st["t"] == 0)          # every window restarted
+        prev = st["r"].clone()
+    est.close()
+
+
+def test_learned_proposer_gains_over_the_plain_method():
+    """Trained on 200 plain iterations of the tiny configuration (one seed),
+    the proposer reaches on a fresh seed the plain method's 64-iteration
+    radiance MSE in fewer iterations and has a lower MSE at 32."""
+    from paper_2504_04411_gb300 import learned
+    train_sc = synth.PlaneScene(nside=64, J=100_000, r0=0.02, step=True, seed=synth.SEED_BASE + 500)
+    tr = learned.run(train_sc, 200)
+    X, Y, M = learned.dataset(tr)
+    blob, _, losses = learned.train(X, Y, M, epochs=20)
+    test_sc = synth.PlaneScene(nside=64, J=100_000, r0=0.02, step=True, seed=synth.SEED_BASE + 600)
+    ref = (test_sc.hitpoints("cuda").pos[:, 0] < 0.5).float()
+    plain = learned.run(test_sc, 64, reference=ref, collect=False)
+    lrn = learned.run(test_sc, 64, blob=blob, threshold=0.5, min_ratio=0.1, reference=ref, collect=False)
+    reach = learned.iterations_to_reach(lrn.mse, plain.mse[-1])
+    assert reach is not None and reach < 64, (reach, lrn.mse[-1], plain.mse[-1])
+    assert lrn.mse[31] < plain.mse[31]
+    # radii stay non-increasing under the proposer
+    assert bool((lrn.r[1:] <= lrn.r[:-1]).all())
