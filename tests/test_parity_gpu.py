@@ -287,3 +287,36 @@ def test_frame_config_full_size_sampled(mapping):
                   check_pairs=False)
     assert rep.diverged <= 3
     torch.cuda.synchronize()
+
+
+def test_vcm_merge_scale_full_size_sampled():
+    """3840x2160 hit points on three faces, 16M RGB light vertices per
+    iteration with log-normal MIS pdf ratios and cosine-distributed incoming
+    directions, r0 = 0.0026 (0.3% of the scene's bounding radius), k = 0.9:
+    the VCM+ merge configuration at full size, 2 iterations, 1000 random hit
+    points against the oracle."""
+    import torch
+    from paper_2504_04411_gb300 import ppm
+    sc = synth.BoxScene(nh=3840 * 2160, J=16_000_000, r0=0.0026, rgb=True, vcm=True,
+                        seed=synth.SEED_BASE + 5)
+    hp = sc.hitpoints("cuda")
+    iters = 2
+    batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
+    p = _params(channels=3, vcm=1, k=0.9)
+    est = ppm.Estimator(hp, sc.r0, params=p)
+    sts = []
+    for ph in batches:
+        est.step(ph)
+        sts.append({k: v.cpu().numpy() for k, v in est.state().items()})
+        assert est.stats().flags == 0
+    L = est.radiance().cpu().numpy()
+    est.close()
+    rng = np.random.default_rng(12)
+    idx = np.sort(rng.choice(hp.n, 1000, replace=False))
+    sub = {k: v[idx] for k, v in hp.numpy().items()}
+    ref = O.run(sub, synth.stack_numpy(batches), sc.r0, iters, k=0.9, vcm=True)
+    sub_states = [{k: v[idx] for k, v in s.items()} for s in sts]
+    rep = compare(sub_states, [{"pairs": 0, "flags": 0}] * iters, L[idx], ref, iters, check_pairs=False)
+    assert rep.diverged <= 3
+    assert ref.pairs.sum() > 50_000
+    torch.cuda.synchronize()
