@@ -102,7 +102,10 @@ typedef struct {
     float n_vm;         /* VCM+: light sub-paths used for merging; 0 = J */
     int32_t mapping;    /* gather traversal: 0 = each thread walks its own cells,
                            1 / 2 = warp walks the union of its 32 hit points'
-                           cells (32 / 64-entry in-disk queues per lane) */
+                           cells (32 / 64-entry in-disk queues per lane),
+                           3 = union walk with one pair queue per warp and
+                           fixed-point group sums (one tested channel; with
+                           rgb_test it runs as 0) */
     int32_t reserved[6];
 } ppm_params;
 

@@ -178,7 +178,8 @@ __global__ void k_batch_geom(int P, const float* __restrict__ rmax, const float*
     g.tmask = tmask;
     g.lb = lb;
     g.pid = (uint32_t)p;
-    g.pad[0] = g.pad[1] = g.pad[2] = 0u;
+    g.psimax = 0.f;
+    g.pad[0] = g.pad[1] = 0u;
     geom[p] = g;
     // Eq. (radiusupdate) bound r_min sqrt((i+1)^(alpha-1)), FP64 then FP32
     bound[p] = (float)((double)rmin[p] * sc->bound_scale);
@@ -191,14 +192,16 @@ __global__ void k_batch_geom(int P, const float* __restrict__ rmax, const float*
 template <int NCH, bool VCM>
 __global__ void __launch_bounds__(256)
 k_batch_pack(const int4* __restrict__ blocks, const PhotonPtrs* __restrict__ ptab,
-             const GridGeom* __restrict__ geom, uint32_t* __restrict__ keys,
+             GridGeom* __restrict__ geom, uint32_t* __restrict__ keys,
              uint32_t* __restrict__ vals, float4* __restrict__ pack0, float4* __restrict__ pack1,
              uint4* __restrict__ pack_aux)
 {
     const int4 B = blocks[blockIdx.x];          // (problem, first local index, count, offset)
     const int i = B.y + threadIdx.x;
-    if (i >= B.z) return;
     const int p = B.x;
+    __shared__ float s_w[8];
+    float vmax = 0.f;
+    if (i < B.z) {
     const PhotonPtrs pt = ptab[p];
     const GridGeom g = geom[p];
     const int64_t o = (int64_t)B.w + i;
@@ -218,6 +221,19 @@ k_batch_pack(const int4* __restrict__ blocks, const PhotonPtrs* __restrict__ pta
     keys[o] = ppm_bucket(ppm_cell_coord(x, g.inv_h), ppm_cell_coord(y, g.inv_h),
                          ppm_cell_coord(z, g.inv_h), g);
     vals[o] = (uint32_t)o;
+    vmax = NCH == 3 ? fmaxf(fmaxf(psi, R), fmaxf(G, Bc)) : psi;
+    }
+    // every block holds photons of one problem: fold its max into that
+    // problem's geometry (scale of the fixed-point group sums)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = vmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, s_w[w]);
+        atomicMax((int*)&geom[p].psimax, __float_as_int(fmaxf(m, 0.f)));
+    }
 }
 
 struct BatchArgs {
@@ -235,11 +251,10 @@ struct BatchArgs {
 };
 
 template <int NCH, int NTC, bool NORMALS, bool VCM, int MAPPING>
-__global__ void __launch_bounds__(kThreads, MAPPING == 0 ? 8 : (MAPPING == 1 ? 6 : 4))
+__global__ void __launch_bounds__(kThreads, MAPPING == 0 ? 8 : (MAPPING == 1 ? 6 : (MAPPING == 2 ? 4 : 5)))
 k_batch_gather(GatherArgs a, BatchArgs bt)
 {
-    __shared__ Smem<NTC> sm;
-    __shared__ typename std::conditional<MAPPING != 0, typename GatherShared<MAPPING>::US, int>::type us_raw;
+    __shared__ BlockShared<NCH, NTC, MAPPING> bsh;
     __shared__ int s_tile;
     for (;;) {
         if (threadIdx.x == 0) s_tile = (int)atomicAdd(bt.head, 1u);
@@ -262,7 +277,7 @@ k_batch_gather(GatherArgs a, BatchArgs bt)
         pr.pid = (uint32_t)p;
         pr.inv_r0 = 0.f;
         pr.log_iter = 0.f;
-        gather_block<NCH, NTC, NORMALS, VCM, MAPPING, true>(a, pr, T.y, T.z, sm, &us_raw);
+        gather_block<NCH, NTC, NORMALS, VCM, MAPPING, true>(a, pr, T.y, T.z, bsh);
     }
 }
 
@@ -321,9 +336,10 @@ template <int NCH, int NTC, bool NORMALS, bool VCM>
 int launch_batch_gather(ppm_batch* b, const GatherArgs& a, const BatchArgs& bt)
 {
     const int m = b->prm.mapping;
-    if (m == 0) k_batch_gather<NCH, NTC, NORMALS, VCM, 0><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
-    else if (m == 1) k_batch_gather<NCH, NTC, NORMALS, VCM, 1><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
-    else k_batch_gather<NCH, NTC, NORMALS, VCM, 2><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
+    if (m == 1) k_batch_gather<NCH, NTC, NORMALS, VCM, 1><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
+    else if (m == 2) k_batch_gather<NCH, NTC, NORMALS, VCM, 2><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
+    else if (m == 3 && NTC == 1) k_batch_gather<NCH, 1, NORMALS, VCM, 3><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
+    else k_batch_gather<NCH, NTC, NORMALS, VCM, 0><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
     PPM_LAUNCH_CHECK();
     return PPM_OK;
 }
@@ -334,9 +350,10 @@ int gather_occupancy(ppm_batch* b)
     int per_sm = 0;
     const int m = b->prm.mapping;
     cudaError_t e;
-    if (m == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gather<NCH, NTC, NORMALS, VCM, 0>, kThreads, 0);
-    else if (m == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gather<NCH, NTC, NORMALS, VCM, 1>, kThreads, 0);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gather<NCH, NTC, NORMALS, VCM, 2>, kThreads, 0);
+    if (m == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gather<NCH, NTC, NORMALS, VCM, 1>, kThreads, 0);
+    else if (m == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gather<NCH, NTC, NORMALS, VCM, 2>, kThreads, 0);
+    else if (m == 3 && NTC == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gather<NCH, 1, NORMALS, VCM, 3>, kThreads, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gather<NCH, NTC, NORMALS, VCM, 0>, kThreads, 0);
     if (e != cudaSuccess) { cudaGetLastError(); return 1; }
     return per_sm > 0 ? per_sm : 1;
 }
@@ -461,7 +478,7 @@ int ppm_batch_create(int32_t n_problems, const ppm_hitpoints* hp, const float* r
     if (!(prm.rmin_ratio >= 0.f && prm.rmin_ratio < 1.f)) return PPM_EINVAL;
     if (prm.channels != 1 && prm.channels != 3) return PPM_EINVAL;
     if (prm.rgb_test && prm.channels != 3) return PPM_EINVAL;
-    if (prm.mapping < 0 || prm.mapping > 2 || prm.n_vm < 0.f) return PPM_EINVAL;
+    if (prm.mapping < 0 || prm.mapping > 3 || prm.n_vm < 0.f) return PPM_EINVAL;
     const int P = n_problems;
     bool any_nq = false, all_nq = true;
     for (int p = 0; p < P; ++p) {

@@ -32,7 +32,14 @@
 //      (broadcast reads, no divergence in the test loop); in-disk hits are
 //      queued per lane and processed in lockstep when a queue fills, so the
 //      long in-disk path runs with most lanes active.  Warps whose union is
-//      wider than a hash block fall back to traversal 0.
+//      wider than a hash block fall back to traversal 0;
+//   3  warp-union with a warp-level pair queue: as 1 above, but in-disk
+//      pairs go to one queue per warp (ballot + prefix) and are classified
+//      32 at a time by any lane, accumulating into the owner's group sums
+//      as 64-bit fixed point with shared-memory atomics (exact and
+//      order-independent, hence deterministic); one tested channel.
+// A context that writes the proposer's features always runs traversal 0,
+// compiled separately so the other kernels carry none of that code.
 #include "ppm_gather_impl.cuh"
 
 namespace {
@@ -51,12 +58,17 @@ template <int NCH, int NTC, bool NORMALS, bool VCM>
 int launch_gather(ppm_ctx* c, const GatherArgs& a, const Prob& pr)
 {
     const unsigned nb = (unsigned)((c->nh + kThreads - 1) / kThreads);
-    if (c->prm.mapping == 0)
-        k_gather_update<NCH, NTC, NORMALS, VCM, 0><<<nb, kThreads, 0, c->stream>>>(a, pr);
-    else if (c->prm.mapping == 1)
+    const int m = c->prm.mapping;
+    if (a.feat)   // features: traversal 0 (results do not depend on the traversal)
+        k_gather_update<NCH, NTC, NORMALS, VCM, 0, true><<<nb, kThreads, 0, c->stream>>>(a, pr);
+    else if (m == 1)
         k_gather_update<NCH, NTC, NORMALS, VCM, 1><<<nb, kThreads, 0, c->stream>>>(a, pr);
-    else
+    else if (m == 2)
         k_gather_update<NCH, NTC, NORMALS, VCM, 2><<<nb, kThreads, 0, c->stream>>>(a, pr);
+    else if (m == 3 && NTC == 1)   // traversal 3 tests one channel
+        k_gather_update<NCH, 1, NORMALS, VCM, 3><<<nb, kThreads, 0, c->stream>>>(a, pr);
+    else
+        k_gather_update<NCH, NTC, NORMALS, VCM, 0><<<nb, kThreads, 0, c->stream>>>(a, pr);
     PPM_LAUNCH_CHECK();
     return PPM_OK;
 }

@@ -258,30 +258,217 @@ __device__ __forceinline__ void drain_queue(const GatherArgs& a, const Hit& H, S
     __syncwarp();
 }
 
-template <int MAPPING>
-struct GatherShared {
-    static constexpr int kQueue = MAPPING == 2 ? 64 : 32;
-    using US = UnionSmem<kQueue>;
+struct Empty {};
+
+// traversal 3: warp-level queue of in-disk pairs, classified by any lane
+constexpr int kPairQ = 160;
+
+struct PairSmem {
+    float4 chunk[kWarps][32];        // staged photon records
+    uint32_t qp[kWarps][kPairQ];     // queued pair: photon index
+    uint8_t qo[kWarps][kPairQ];      //              owning lane
+    float4 hP[kWarps][32];           // the warp's hit points: x, y, z, normal
+    float4 hU[kWarps][32];           //   u, rho_vm
+    float4 hV[kWarps][32];           //   v, rho_vc
+    float2 hR[kWarps][32];           //   r^2, 1/eta
 };
+
+// Group sums as 64-bit fixed point (psi * 2^40 / psi_max): integer adds are
+// exact and order-independent, so lanes of a warp can add into any hit
+// point's sums with shared-memory atomics and the result stays bit-for-bit
+// deterministic (and is a correctly rounded sum, unlike sequential FP32).
+template <int NCH>
+struct FixSmem {
+    unsigned long long S[PPM_NG][kThreads];
+    unsigned long long Q[PPM_NG][kThreads];
+    uint32_t c[PPM_NG][kThreads];
+    unsigned long long F[NCH == 3 ? 3 : 1][kThreads];   // RGB flux (luminance test)
+};
+
+template <int NCH, int NTC, int MAPPING>
+struct BlockShared {
+    typename std::conditional<MAPPING == 3, Empty, Smem<NTC>>::type sm;
+    typename std::conditional<MAPPING == 1 || MAPPING == 2, UnionSmem<MAPPING == 2 ? 64 : 32>, Empty>::type us;
+    typename std::conditional<MAPPING == 3, PairSmem, Empty>::type ps;
+    typename std::conditional<MAPPING == 3, FixSmem<NCH>, Empty>::type fx;
+};
+
+// this iteration's sums of one hit point, read where they are kept
+template <int NCH, int NTC, int MAPPING>
+struct GroupSums;
+
+struct FixScale {
+    float s1;    // psi -> fixed point: psi * 2^40 / psi_max
+    float t;     // psi -> q with q^2 the fixed point of psi^2: psi * 2^20 / psi_max
+    float dS;    // fixed point -> sum of psi:    psi_max * 2^-40
+    float dQ;    // fixed point -> sum of psi^2: (psi_max * 2^-20)^2
+};
+
+template <int NCH, int NTC, int MAPPING>
+struct GroupSums {
+    const BlockShared<NCH, NTC, MAPPING>& b;
+    int tid;
+    FixScale fs;
+    __device__ __forceinline__ float S(int c, int g) const
+    {
+        if constexpr (MAPPING == 3) return __fmul_rn(__ull2float_rn(b.fx.S[g][tid]), fs.dS);
+        else return b.sm.SQ[c][g][tid].x;
+    }
+    __device__ __forceinline__ float Q(int c, int g) const
+    {
+        if constexpr (MAPPING == 3) return __fmul_rn(__ull2float_rn(b.fx.Q[g][tid]), fs.dQ);
+        else return b.sm.SQ[c][g][tid].y;
+    }
+    __device__ __forceinline__ uint32_t C(int g) const
+    {
+        if constexpr (MAPPING == 3) return b.fx.c[g][tid];
+        else return b.sm.c[g][tid];
+    }
+};
+
+__device__ __forceinline__ FixScale fix_scale(float psimax)
+{
+    const float pm = fmaxf(psimax, 1e-25f);
+    FixScale f;
+    f.s1 = 1099511627776.0f / pm;
+    f.t = 1048576.0f / pm;
+    f.dS = pm * (1.0f / 1099511627776.0f);
+    const float r = pm * (1.0f / 1048576.0f);
+    f.dQ = r * r;
+    return f;
+}
+
+// traversal 3: everything after the disk test, accumulated into hit point
+// `slot` of the block with integer atomics
+template <int NCH, bool NORMALS, bool VCM, bool BATCH>
+__device__ __forceinline__ void gather_pair_fix(const GatherArgs& a, const Hit& H, FixSmem<NCH>& fx, int slot,
+                                                const FixScale& fs, uint32_t p, const float4& X,
+                                                float dx, float dy, float dz)
+{
+    uint4 A = make_uint4(0u, 0u, 0u, 0u);
+    if constexpr (NORMALS || VCM || BATCH) A = __ldg(a.aux + p);
+    if constexpr (BATCH) {
+        if (A.w != H.pid) return;
+    }
+    if constexpr (NORMALS) {
+        if (__dp4a((int)A.x, (int)H.nqh, 0) <= kNormalDotMin) return;
+    }
+    const float yu = fmaf(dz, H.U.z, fmaf(dy, H.U.y, __fmul_rn(dx, H.U.x)));
+    const float yv = fmaf(dz, H.V.z, fmaf(dy, H.V.y, __fmul_rn(dx, H.V.x)));
+    const int g = pair_group(yu, yv, H.r2);
+    float w = 1.f;
+    float4 X1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (NCH == 3 || VCM) X1 = __ldg(a.rec1 + p);
+    if constexpr (VCM) {
+        const int cd = __dp4a((int)A.y, (int)H.nqh, 0);
+        const float cosl = cd > 0 ? __fmul_rn((float)cd, 1.0f / 16129.0f) : 0.f;
+        const float r_vm = fmaf(H.U.w, __fmul_rn(cosl, 0.318309886f), X1.w);
+        const float r_vc = __fadd_rn(H.V.w, __uint_as_float(A.z));
+        w = __frcp_rn(1.f + r_vm + r_vc * H.inv_eta);
+    }
+    const float psi = VCM ? __fmul_rn(w, X.w) : X.w;
+    const float q = psi * fs.t;
+    atomicAdd(&fx.c[g][slot], 1u);
+    atomicAdd(&fx.S[g][slot], (unsigned long long)__float2ull_rn(psi * fs.s1));
+    atomicAdd(&fx.Q[g][slot], (unsigned long long)__float2ull_rn(q * q));
+    if constexpr (NCH == 3) {
+        atomicAdd(&fx.F[0][slot], (unsigned long long)__float2ull_rn((VCM ? __fmul_rn(w, X1.x) : X1.x) * fs.s1));
+        atomicAdd(&fx.F[1][slot], (unsigned long long)__float2ull_rn((VCM ? __fmul_rn(w, X1.y) : X1.y) * fs.s1));
+        atomicAdd(&fx.F[2][slot], (unsigned long long)__float2ull_rn((VCM ? __fmul_rn(w, X1.z) : X1.z) * fs.s1));
+    }
+}
+
+// traversal 3: classify the warp's queued pairs, 32 at a time, any lane
+template <int NCH, bool NORMALS, bool VCM, bool BATCH>
+__device__ __forceinline__ void drain_pairs(const GatherArgs& a, PairSmem& ps, FixSmem<NCH>& fx,
+                                            const FixScale& fs, uint32_t pid, int w, int lane, int qn)
+{
+    for (int e0 = 0; e0 < qn; e0 += 32) {
+        const int e = e0 + lane;
+        if (e < qn) {
+            const uint32_t p = ps.qp[w][e];
+            const int o = ps.qo[w][e];
+            Hit Ho;
+            Ho.P = ps.hP[w][o];
+            Ho.U = ps.hU[w][o];
+            Ho.V = ps.hV[w][o];
+            const float2 R = ps.hR[w][o];
+            Ho.r2 = R.x;
+            Ho.inv_eta = R.y;
+            Ho.nqh = __float_as_uint(Ho.P.w);
+            Ho.pid = pid;
+            const float4 X = __ldg(a.rec0 + p);
+            float dx, dy, dz;
+            in_disk(Ho, X, dx, dy, dz);
+            gather_pair_fix<NCH, NORMALS, VCM, BATCH>(a, Ho, fx, w * 32 + o, fs, p, X, dx, dy, dz);
+        }
+    }
+    __syncwarp();
+}
+
+// the 12 features of the learned proposer for hit point h (out of line:
+// only contexts with features enabled pay for its registers)
+template <int NCH, int NTC, int MAPPING>
+__device__ __noinline__ void write_features(const GatherArgs& a, const Prob& pr,
+                                            const GroupSums<NCH, NTC, MAPPING>& gs, int64_t h,
+                                            const float* Sg, float Ssum, float dev2, float F, float fc,
+                                            float r, int32_t tp)
+{
+    const int64_t nh = a.nh;
+    uint32_t C = 0, cmax = 0, empty = 0;
+    float smax = 0.f, smin = Sg[0];
+#pragma unroll
+    for (int g = 0; g < PPM_NG; ++g) {
+        const uint32_t cg = a.cnt[g * nh + h] + gs.C(g);
+        C += cg;
+        cmax = max(cmax, cg);
+        empty += cg == 0u;
+        smax = fmaxf(smax, Sg[g]);
+        smin = fminf(smin, Sg[g]);
+    }
+    const float f[kFeatures] = {
+        log1pf((float)C), log1pf((float)tp), pr.log_iter, r * pr.inv_r0,
+        logf(fmaxf(r * pr.inv_r0, 1e-30f)), log1pf(F), F / fc,
+        Ssum > 0.f ? smax / Ssum : 0.f, Ssum > 0.f ? smin / Ssum : 0.f,
+        (float)empty * (1.0f / PPM_NG),
+        Ssum > 0.f ? sqrtf(dev2 * (1.0f / PPM_NG)) / (Ssum * (1.0f / PPM_NG)) : 0.f,
+        C > 0u ? (float)cmax / (float)C : 0.f};
+#pragma unroll
+    for (int q = 0; q < kFeatures; ++q) a.feat[(int64_t)q * nh + h] = f[q];
+}
 
 // The hit points [h0, h_end) (at most one block's worth, h0 + tid for this
 // thread) of problem pr: gather, test, update; block-wide reductions into
 // pr's counters.  Ends with a block barrier, so it can be called in a loop.
-template <int NCH, int NTC, bool NORMALS, bool VCM, int MAPPING, bool BATCH>
+// FEAT: also write the proposer's features (a separate instantiation: the
+// call alone costs the feature-free kernel about 10% through register
+// allocation in the cell walk)
+template <int NCH, int NTC, bool NORMALS, bool VCM, int MAPPING, bool BATCH, bool FEAT = false>
 __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr, int64_t h0,
-                                             int64_t h_end, Smem<NTC>& sm, void* us_raw)
+                                             int64_t h_end, BlockShared<NCH, NTC, MAPPING>& bsh)
 {
-    using US = typename GatherShared<MAPPING>::US;
-    constexpr int kQueue = GatherShared<MAPPING>::kQueue;
+    static_assert(MAPPING != 3 || NTC == 1, "traversal 3 tests one channel");
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int64_t h = h0 + tid;
     const bool live = h < h_end;
-
+    constexpr int kQueue = MAPPING == 2 ? 64 : 32;
+    auto& sm = bsh.sm;
+    if constexpr (MAPPING != 3) {
 #pragma unroll
-    for (int g = 0; g < PPM_NG; ++g) {
-        sm.c[g][tid] = 0u;
+        for (int g = 0; g < PPM_NG; ++g) {
+            sm.c[g][tid] = 0u;
 #pragma unroll
-        for (int c = 0; c < NTC; ++c) sm.SQ[c][g][tid] = make_float2(0.f, 0.f);
+            for (int c = 0; c < NTC; ++c) sm.SQ[c][g][tid] = make_float2(0.f, 0.f);
+        }
+    } else {
+#pragma unroll
+        for (int g = 0; g < PPM_NG; ++g) {
+            bsh.fx.S[g][tid] = 0ull;
+            bsh.fx.Q[g][tid] = 0ull;
+            bsh.fx.c[g][tid] = 0u;
+        }
+#pragma unroll
+        for (int c = 0; c < (NCH == 3 ? 3 : 1); ++c) bsh.fx.F[c][tid] = 0ull;
     }
 
     Acc<NCH> acc;
@@ -289,8 +476,11 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
     for (int c = 0; c < NCH; ++c) { acc.phi[c] = 0.f; acc.comp[c] = 0.f; }
     Hit H;
     H.r = 0.f; H.r2 = 0.f;
-    const GridGeom G = *pr.geom;
-    H.pid = pr.pid;
+    GridGeom G = *pr.geom;
+    // one problem: problem id 0 as a constant, so the bucket hash keeps no
+    // register for it through the cell walk
+    if constexpr (!BATCH) G.pid = 0u;
+    H.pid = BATCH ? pr.pid : 0u;
     CellBox b{INT_MAX, INT_MIN, INT_MAX, INT_MIN, INT_MAX, INT_MIN};
     if (live) {
         H.P = a.hp_pos[h];
@@ -310,10 +500,100 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
         H.r2 = -1.f;                      // no photon passes d2 <= -1
     }
 
+    const FixScale fs = fix_scale(MAPPING == 3 ? G.psimax : 1.f);
     if constexpr (MAPPING == 0) {
         if (live) gather_own<NCH, NTC, NORMALS, VCM, BATCH>(a, H, G, b, sm, tid, acc);
+    } else if constexpr (MAPPING == 3) {
+        PairSmem& ps = bsh.ps;
+        auto& fx = bsh.fx;
+        const unsigned full = 0xffffffffu;
+        const unsigned lt = (1u << lane) - 1u;
+        ps.hP[w][lane] = H.P;
+        ps.hU[w][lane] = H.U;
+        ps.hV[w][lane] = H.V;
+        ps.hR[w][lane] = make_float2(H.r2, H.inv_eta);
+        __syncwarp();
+        const int X0 = __reduce_min_sync(full, b.ix0), X1 = __reduce_max_sync(full, b.ix1);
+        const int Y0 = __reduce_min_sync(full, b.iy0), Y1 = __reduce_max_sync(full, b.iy1);
+        const int Z0 = __reduce_min_sync(full, b.iz0), Z1 = __reduce_max_sync(full, b.iz1);
+        const int B = 1 << G.lb;
+        const bool any_live = __any_sync(full, live);
+        if (any_live && (X1 - X0 >= B || Y1 - Y0 >= B || Z1 - Z0 >= B)) {
+            // union wider than a hash block: every lane walks its own cells
+            // and queues only its own pairs (its own slots: no conflicts)
+            if (live) {
+                int bx1 = b.ix1, by1 = b.iy1, bz1 = b.iz1;
+                if (b.ix1 - b.ix0 >= B || b.iy1 - b.iy0 >= B || b.iz1 - b.iz0 >= B) {
+                    atomicOr(a.err, 1);
+                    bx1 = min(bx1, b.ix0 + B - 1); by1 = min(by1, b.iy0 + B - 1); bz1 = min(bz1, b.iz0 + B - 1);
+                }
+                for (int iz = b.iz0; iz <= bz1; ++iz)
+                    for (int iy = b.iy0; iy <= by1; ++iy) {
+                        int ix = b.ix0;
+                        while (ix <= bx1) {
+                            const int ixe = min(bx1, ix | (B - 1));
+                            const uint32_t b0 = ppm_bucket(ix, iy, iz, G);
+                            const uint32_t s = __ldg(a.cell_start + b0);
+                            const uint32_t e = __ldg(a.cell_start + b0 + (uint32_t)(ixe - ix) + 1u);
+                            acc.cand += e - s;
+                            for (uint32_t p = s; p < e; ++p) {
+                                const float4 X = __ldg(a.rec0 + p);
+                                float dx, dy, dz;
+                                if (in_disk(H, X, dx, dy, dz))
+                                    gather_pair_fix<NCH, NORMALS, VCM, BATCH>(a, H, fx, tid, fs, p, X, dx, dy, dz);
+                            }
+                            ix = ixe + 1;
+                        }
+                    }
+            }
+        } else if (any_live) {
+            int qn = 0;                     // warp-uniform queue length
+            for (int iz = Z0; iz <= Z1; ++iz) {
+                for (int iy = Y0; iy <= Y1; ++iy) {
+                    const bool need = live && b.iy0 <= iy && iy <= b.iy1 && b.iz0 <= iz && iz <= b.iz1;
+                    if (!__any_sync(full, need)) continue;
+                    const int rx0 = __reduce_min_sync(full, need ? b.ix0 : INT_MAX);
+                    const int rx1 = __reduce_max_sync(full, need ? b.ix1 : INT_MIN);
+                    int ix = rx0;
+                    while (ix <= rx1) {
+                        const int ixe = min(rx1, ix | (B - 1));
+                        const uint32_t b0 = ppm_bucket(ix, iy, iz, G);
+                        const uint32_t s = __ldg(a.cell_start + b0);
+                        const uint32_t e = __ldg(a.cell_start + b0 + (uint32_t)(ixe - ix) + 1u);
+                        if (need) acc.cand += e - s;
+                        for (uint32_t base = s; base < e; base += 32u) {
+                            const int n = (int)min(32u, e - base);
+                            if (lane < n) ps.chunk[w][lane] = __ldg(a.rec0 + base + lane);
+                            __syncwarp();
+                            for (int j = 0; j < n; ++j) {
+                                const float4 X = ps.chunk[w][j];
+                                float dx, dy, dz;
+                                const bool in = in_disk(H, X, dx, dy, dz);
+                                const unsigned bal = __ballot_sync(full, in);
+                                if (in) {
+                                    const int pos = qn + __popc(bal & lt);
+                                    ps.qp[w][pos] = base + (uint32_t)j;
+                                    ps.qo[w][pos] = (uint8_t)lane;
+                                }
+                                qn += __popc(bal);
+                                if (qn > kPairQ - 32) {
+                                    __syncwarp();
+                                    drain_pairs<NCH, NORMALS, VCM, BATCH>(a, ps, fx, fs, pr.pid, w, lane, qn);
+                                    qn = 0;
+                                }
+                            }
+                            __syncwarp();
+                        }
+                        ix = ixe + 1;
+                    }
+                }
+            }
+            __syncwarp();
+            drain_pairs<NCH, NORMALS, VCM, BATCH>(a, ps, fx, fs, pr.pid, w, lane, qn);
+        }
     } else {
-        US& us = *reinterpret_cast<US*>(us_raw);
+        using US = UnionSmem<kQueue>;
+        US& us = bsh.us;
         const unsigned full = 0xffffffffu;
         const int X0 = __reduce_min_sync(full, b.ix0), X1 = __reduce_max_sync(full, b.ix1);
         const int Y0 = __reduce_min_sync(full, b.iy0), Y1 = __reduce_max_sync(full, b.iy1);
@@ -370,6 +650,16 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
         }
     }
 
+    // this iteration's sums of this thread's hit point
+    const GroupSums<NCH, NTC, MAPPING> gs{bsh, tid, fs};
+    if constexpr (MAPPING == 3) {
+        __syncwarp();
+        if constexpr (NCH == 3) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc.phi[c] = __fmul_rn(__ull2float_rn(bsh.fx.F[c][tid]), fs.dS);
+        }
+    }
+
     // ---------------- epilogue: F-test, estimate, radius update ----------
     float r_new = 0.f;
     unsigned long long rej = 0, pairs = 0;
@@ -391,9 +681,8 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
 #pragma unroll
             for (int g = 0; g < PPM_NG; ++g) {
                 const int64_t o = ((int64_t)c * PPM_NG + g) * nh + h;
-                const float2 v = sm.SQ[c][g][tid];
-                Sg[g] = a.S[o] + v.x;
-                Qsum += a.Q[o] + v.y;
+                Sg[g] = a.S[o] + gs.S(c, g);
+                Qsum += a.Q[o] + gs.Q(c, g);
                 Ssum += Sg[g];
                 S2 = fmaf(Sg[g], Sg[g], S2);
             }
@@ -408,29 +697,8 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
             if (ssw > 0.f) F = (dev2 / ssw) * (((float)PPM_NG * (m - 1.0f)) / ((float)(PPM_NG - 1) * m));
             if (c == 0) F0 = F;
             if (ssw > 0.f && (double)F > pr.fc[tpi]) reject = true;
-            if (c == 0 && a.feat) {
-                uint32_t C = 0, cmax = 0, empty = 0;
-                float smax = 0.f, smin = Sg[0];
-#pragma unroll
-                for (int g = 0; g < PPM_NG; ++g) {
-                    const uint32_t cg = a.cnt[g * nh + h] + sm.c[g][tid];
-                    C += cg;
-                    cmax = max(cmax, cg);
-                    empty += cg == 0u;
-                    smax = fmaxf(smax, Sg[g]);
-                    smin = fminf(smin, Sg[g]);
-                }
-                const float fc = (float)pr.fc[tpi];
-                const float f[kFeatures] = {
-                    log1pf((float)C), log1pf((float)tp), pr.log_iter, r * pr.inv_r0,
-                    logf(fmaxf(r * pr.inv_r0, 1e-30f)), log1pf(F), F / fc,
-                    Ssum > 0.f ? smax / Ssum : 0.f, Ssum > 0.f ? smin / Ssum : 0.f,
-                    (float)empty * (1.0f / PPM_NG),
-                    Ssum > 0.f ? sqrtf(dev2 * (1.0f / PPM_NG)) / (Ssum * (1.0f / PPM_NG)) : 0.f,
-                    C > 0u ? (float)cmax / (float)C : 0.f};
-#pragma unroll
-                for (int q = 0; q < kFeatures; ++q) a.feat[(int64_t)q * nh + h] = f[q];
-            }
+            if constexpr (FEAT)
+                if (c == 0) write_features<NCH, NTC, MAPPING>(a, pr, gs, h, Sg, Ssum, dev2, F, (float)pr.fc[tpi], r, tp);
         }
         // Eq. (progressive-VCM-estimator): kernel estimate with this r_i;
         // Phi_i = sum over groups of this iteration's psi sums unless RGB
@@ -440,7 +708,7 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
             for (int c = 0; c < NCH; ++c) {
                 float f = 0.f;
 #pragma unroll
-                for (int g = 0; g < PPM_NG; ++g) f += sm.SQ[c][g][tid].x;
+                for (int g = 0; g < PPM_NG; ++g) f += gs.S(c, g);
                 acc.phi[c] = f;
             }
         }
@@ -448,7 +716,7 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
 #pragma unroll
         for (int c = 0; c < NCH; ++c) a.tau[h * NCH + c] += (double)__fmul_rn(acc.phi[c], inv_area);
 #pragma unroll
-        for (int g = 0; g < PPM_NG; ++g) pairs += sm.c[g][tid];
+        for (int g = 0; g < PPM_NG; ++g) pairs += gs.C(g);
         a.F[h] = F0;
         if (reject) {
             r_new = fmaxf(__fmul_rn(pr.k, r), pr.bound);
@@ -469,15 +737,14 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
             r_new = r;
             a.t[h] = tp;
 #pragma unroll
-            for (int g = 0; g < PPM_NG; ++g) a.cnt[g * nh + h] += sm.c[g][tid];
+            for (int g = 0; g < PPM_NG; ++g) a.cnt[g * nh + h] += gs.C(g);
 #pragma unroll
             for (int c = 0; c < NTC; ++c)
 #pragma unroll
                 for (int g = 0; g < PPM_NG; ++g) {
                     const int64_t o = ((int64_t)c * PPM_NG + g) * nh + h;
-                    const float2 v = sm.SQ[c][g][tid];
-                    a.S[o] += v.x;
-                    a.Q[o] += v.y;
+                    a.S[o] += gs.S(c, g);
+                    a.Q[o] += gs.Q(c, g);
                 }
         }
     }
@@ -510,14 +777,13 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
 }
 
 // one context: one block per 128 hit points
-template <int NCH, int NTC, bool NORMALS, bool VCM, int MAPPING>
-__global__ void __launch_bounds__(kThreads, MAPPING == 0 ? 8 : (MAPPING == 1 ? 6 : 4))
+template <int NCH, int NTC, bool NORMALS, bool VCM, int MAPPING, bool FEAT = false>
+__global__ void __launch_bounds__(kThreads, MAPPING == 0 ? 8 : (MAPPING == 1 ? 6 : (MAPPING == 2 ? 4 : 5)))
 k_gather_update(GatherArgs a, Prob pr)
 {
-    __shared__ Smem<NTC> sm;
-    __shared__ typename std::conditional<MAPPING != 0, typename GatherShared<MAPPING>::US, int>::type us_raw;
+    __shared__ BlockShared<NCH, NTC, MAPPING> bsh;
     const int64_t h0 = (int64_t)blockIdx.x * kThreads;
-    gather_block<NCH, NTC, NORMALS, VCM, MAPPING, false>(a, pr, h0, a.nh, sm, &us_raw);
+    gather_block<NCH, NTC, NORMALS, VCM, MAPPING, false, FEAT>(a, pr, h0, a.nh, bsh);
 }
 
 }  // namespace

@@ -24,7 +24,8 @@ __global__ void k_grid_geom(GridGeom* __restrict__ g, const float* __restrict__ 
     o.tmask = tmask;
     o.lb = lb;
     o.pid = 0u;
-    o.pad[0] = o.pad[1] = o.pad[2] = 0u;
+    o.psimax = 0.f;
+    o.pad[0] = o.pad[1] = 0u;
     *g = o;
 }
 
@@ -34,25 +35,43 @@ __device__ __forceinline__ float lum709(float R, float G, float B)
     return fmaf(0.0722f, B, fmaf(0.7152f, G, __fmul_rn(0.2126f, R)));
 }
 
+// block-wide max of v >= 0 folded into *dst (float bits order as ints)
+__device__ __forceinline__ void block_max_into(float v, float* dst)
+{
+    __shared__ float s_w[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, s_w[w]);
+        atomicMax((int*)dst, __float_as_int(m));
+    }
+}
+
 template <int NCH, bool AUX, bool VCM>
 __global__ void __launch_bounds__(256)
 k_pack_keys(int64_t n, const float* __restrict__ pos, const float* __restrict__ flux,
             const uint32_t* __restrict__ nq, const float* __restrict__ rho,
-            const uint32_t* __restrict__ wq, const GridGeom* __restrict__ geom,
+            const uint32_t* __restrict__ wq, GridGeom* __restrict__ geom,
             uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
             float4* __restrict__ pack0, float4* __restrict__ pack1, uint4* __restrict__ pack_aux)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
     const GridGeom g = *geom;
+    float vmax = 0.f;
+    if (i < n) {
     const float x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
     float R, G = 0.f, B = 0.f, psi;
     if (NCH == 3) {
         R = flux[3 * i]; G = flux[3 * i + 1]; B = flux[3 * i + 2];
         psi = lum709(R, G, B);
+        vmax = fmaxf(fmaxf(psi, R), fmaxf(G, B));
     } else {
         R = flux[i];
         psi = R;
+        vmax = psi;
     }
     pack0[i] = make_float4(x, y, z, psi);
     if (NCH == 3 || VCM)
@@ -65,6 +84,10 @@ k_pack_keys(int64_t n, const float* __restrict__ pos, const float* __restrict__ 
     const int iz = ppm_cell_coord(z, g.inv_h);
     keys[i] = ppm_bucket(ix, iy, iz, g);
     vals[i] = (uint32_t)i;
+    }
+    // largest tested value (and flux channel) of the iteration: the scale of
+    // the gather's fixed-point group sums
+    block_max_into(fmaxf(vmax, 0.f), &geom->psimax);
 }
 
 // One thread per sorted photon i in [0, n]: fills the buckets between the
@@ -148,7 +171,7 @@ int ppm_grid_build(ppm_ctx* c, const ppm_photons* ph)
     if (rc) return rc;
     // hash blocks of 4^3 cells suffice for one sphere (<= 4 cells per axis at
     // cell_factor >= 1); the warp-union traversal and cell_factor < 1 need 8^3
-    const int lb = (c->prm.cell_factor >= 1.0f && c->prm.mapping == 0) ? 2 : 3;
+    const int lb = (c->prm.cell_factor >= 1.0f && c->prm.mapping == 0) ? 2 : 3;   // union traversals: 8^3
     c->tbits = ppm_table_bits(n, lb);
     const uint32_t T = 1u << c->tbits;
     if ((int64_t)T + 1 > c->cs_cap) {

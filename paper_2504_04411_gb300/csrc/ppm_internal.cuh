@@ -45,7 +45,8 @@ struct GridGeom {
     uint32_t tmask;    // T - 1
     int32_t lb;        // log2 of the block edge in cells (2 or 3)
     uint32_t pid;      // problem id mixed into the hash (0 for one problem)
-    uint32_t pad[3];
+    float psimax;      // largest tested value psi of the grid's photons (>= 0)
+    uint32_t pad[2];
 };
 
 __device__ __forceinline__ uint32_t ppm_fmix32(uint32_t x)

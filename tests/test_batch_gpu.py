@@ -51,7 +51,7 @@ def _run_batch(scenes, iters, params, cfs=None):
     return hps, phs, states, stats, L, graph
 
 
-@pytest.mark.parametrize("mapping", [0, 1])
+@pytest.mark.parametrize("mapping", [0, 1, 3])
 def test_batch_matches_oracle_per_problem(mapping):
     scenes = _problems()
     iters = 4
@@ -65,7 +65,7 @@ def test_batch_matches_oracle_per_problem(mapping):
         assert rep.diverged <= 2
 
 
-@pytest.mark.parametrize("mapping", [0, 1])
+@pytest.mark.parametrize("mapping", [0, 1, 3])
 def test_batch_bit_identical_to_single_contexts(mapping):
     import torch
     from paper_2504_04411_gb300 import ppm
