@@ -255,7 +255,7 @@ int ppm_mlp_pack(const float* master, void* blob, void* stream);
  * factor a problem's results are bit-identical to a context's.  One
  * iteration of all of them is one grid build over all photons (the
  * problem id is mixed into the bucket hash and checked in the gather) and
- * ONE persistent gather launch whose resident blocks pull 128-hit-point
+ * ONE persistent gather launch whose resident blocks pull 64-hit-point
  * tiles from an atomic queue, heaviest problems first.  From the second
  * iteration on, the whole iteration is replayed as a CUDA graph on a
  * private stream ordered after the caller's stream. */

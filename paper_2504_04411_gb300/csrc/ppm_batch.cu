@@ -4,7 +4,7 @@
 //   one pack pass over all photons (the problem id is mixed into the bucket
 //   hash and carried in every record), one stable radix sort, one cell-range
 //   pass, one permute, and ONE persistent gather launch: resident blocks pull
-//   tiles of 128 hit points of one problem from an atomic queue, heaviest
+//   tiles of kThreads hit points of one problem from an atomic queue, heaviest
 //   problems first, and run the same gather / F-test / update as a single
 //   context (bit-identical results for the same mapping and cell factor).
 // From the second iteration on the whole sequence is replayed as a CUDA
@@ -189,7 +189,8 @@ __global__ void k_batch_geom(int P, const float* __restrict__ rmax, const float*
     counters[4 * p + 2] = 0ull;
 }
 
-template <int NCH, bool VCM>
+// PSIMAX: also record each problem's largest tested value (traversal 3 only)
+template <int NCH, bool VCM, bool PSIMAX>
 __global__ void __launch_bounds__(256)
 k_batch_pack(const int4* __restrict__ blocks, const PhotonPtrs* __restrict__ ptab,
              GridGeom* __restrict__ geom, uint32_t* __restrict__ keys,
@@ -225,14 +226,16 @@ k_batch_pack(const int4* __restrict__ blocks, const PhotonPtrs* __restrict__ pta
     }
     // every block holds photons of one problem: fold its max into that
     // problem's geometry (scale of the fixed-point group sums)
+    if constexpr (PSIMAX) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = vmax;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float m = 0.f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, s_w[w]);
-        atomicMax((int*)&geom[p].psimax, __float_as_int(fmaxf(m, 0.f)));
+        for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = vmax;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float m = 0.f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, s_w[w]);
+            atomicMax((int*)&geom[p].psimax, __float_as_int(fmaxf(m, 0.f)));
+        }
     }
 }
 
@@ -251,7 +254,7 @@ struct BatchArgs {
 };
 
 template <int NCH, int NTC, bool NORMALS, bool VCM, int MAPPING>
-__global__ void __launch_bounds__(kThreads, MAPPING == 0 ? 8 : (MAPPING == 1 ? 6 : (MAPPING == 2 ? 4 : 5)))
+__global__ void __launch_bounds__(kThreads, kMinBlocks<MAPPING>)
 k_batch_gather(GatherArgs a, BatchArgs bt)
 {
     __shared__ BlockShared<NCH, NTC, MAPPING> bsh;
@@ -420,12 +423,17 @@ int enqueue_iteration(ppm_batch* b)
     const int64_t n = b->np_total;
     if (n > 0) {
         const bool vcm = b->prm.vcm != 0;
+        const bool pm = b->prm.mapping == 3;
+        auto pack = [&](auto kern) {
+            kern<<<b->npack, 256, 0, st>>>(b->pack_blocks, b->ptab_d, b->geom, b->sort.keys, b->sort.vals,
+                                           b->pack0, b->pack1, b->pack_aux);
+        };
         if (b->nch == 3) {
-            if (vcm) k_batch_pack<3, true><<<b->npack, 256, 0, st>>>(b->pack_blocks, b->ptab_d, b->geom, b->sort.keys, b->sort.vals, b->pack0, b->pack1, b->pack_aux);
-            else k_batch_pack<3, false><<<b->npack, 256, 0, st>>>(b->pack_blocks, b->ptab_d, b->geom, b->sort.keys, b->sort.vals, b->pack0, b->pack1, b->pack_aux);
+            if (vcm) pm ? pack(k_batch_pack<3, true, true>) : pack(k_batch_pack<3, true, false>);
+            else pm ? pack(k_batch_pack<3, false, true>) : pack(k_batch_pack<3, false, false>);
         } else {
-            if (vcm) k_batch_pack<1, true><<<b->npack, 256, 0, st>>>(b->pack_blocks, b->ptab_d, b->geom, b->sort.keys, b->sort.vals, b->pack0, b->pack1, b->pack_aux);
-            else k_batch_pack<1, false><<<b->npack, 256, 0, st>>>(b->pack_blocks, b->ptab_d, b->geom, b->sort.keys, b->sort.vals, b->pack0, b->pack1, b->pack_aux);
+            if (vcm) pm ? pack(k_batch_pack<1, true, true>) : pack(k_batch_pack<1, true, false>);
+            else pm ? pack(k_batch_pack<1, false, true>) : pack(k_batch_pack<1, false, false>);
         }
         PPM_LAUNCH_CHECK();
         ++launches;
@@ -585,7 +593,7 @@ int ppm_batch_create(int32_t n_problems, const ppm_hitpoints* hp, const float* r
             rc = ppm_fcrit_fill(tab, 1, kFcCap, (double)J[p], prm.alpha_f, st);
         }
         if (rc) break;
-        // tiles of 128 hit points, problems with the most photons per disk
+        // tiles of kThreads hit points, problems with the most photons per disk
         // (J r0^2) first so the long tiles start early
         std::vector<int> order(P);
         for (int p = 0; p < P; ++p) order[p] = p;

@@ -152,6 +152,28 @@ def test_box_scene_vcm_merge_weights(rgb, mapping):
     compare(states, stats, L, ref, iters)
 
 
+@pytest.mark.parametrize("mapping", MAPPINGS)
+@pytest.mark.parametrize("offset", [(300.25, -512.5, 77.0), (-3000.0, 1500.0, 2000.0)])
+def test_translated_box_scene(offset, mapping):
+    """The box scene moved far from the origin: FP32 coordinates are coarse
+    there (about 2.4e-4 apart at 3000), which the cell cull's margins and the
+    trimmed row ranges must cover; every pair the disk test accepts is still
+    found, as the oracle's brute force says."""
+    import dataclasses
+    import torch
+    sc = _box(seed=4)
+    iters = 4
+    d = torch.tensor(offset, dtype=torch.float32, device="cuda")
+    hp = sc.hitpoints("cuda")
+    hp = dataclasses.replace(hp, pos=(hp.pos + d).contiguous())
+    batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
+    batches = [dataclasses.replace(b, pos=(b.pos + d).contiguous()) for b in batches]
+    states, stats, L = run_gpu(hp, batches, sc.r0, params=_params(mapping=mapping))
+    ref = O.run(hp.numpy(), synth.stack_numpy(batches), sc.r0, iters)
+    rep = compare(states, stats, L, ref, iters)
+    assert rep.diverged <= 3
+
+
 # ------------------------------------------------------------ edge cases ---
 def test_empty_iterations_and_single_hit_point():
     import torch
