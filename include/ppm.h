@@ -186,6 +186,25 @@ int ppm_set_iteration(ppm_ctx* ctx, int32_t iter);
 /* Counters of the last iteration; waits for the stream. */
 int ppm_stats(ppm_ctx* ctx, ppm_iter_stats* out);
 
+/* One whole iteration fed from HOST memory: the grid build of
+ * ppm_build_grid and the gather/test/update of ppm_gather_test_update for
+ * iteration iter (Sec. 5.1 steps 1-4), with host_ph's arrays (same layout
+ * and rules as ppm_photons, host pointers) first copied into one of two
+ * context-owned device buffers, used in turn, on a private copy stream.
+ * With page-locked host arrays the copy of iteration i overlaps the gather
+ * of iteration i - 1; pageable arrays work, without that overlap.  After
+ * the gather the iteration's counters are copied to page-locked memory.
+ * Returns without waiting.  The caller keeps host_ph's arrays unchanged
+ * until ppm_stats_host has returned for this iteration (or the context's
+ * stream has been synchronized).  PPM_ESTATE unless iter = last + 1.  The
+ * device buffers grow (with one synchronization) when n grows. */
+int ppm_iterate_host(ppm_ctx* ctx, const ppm_photons* host_ph, int32_t iter);
+
+/* Counters of host-fed iteration iter, which must be one of the last two
+ * ppm_iterate_host iterations (PPM_ESTATE otherwise): waits only for that
+ * iteration's counter copy, not for later work.  gather_ms is -1. */
+int ppm_stats_host(ppm_ctx* ctx, int32_t iter, ppm_iter_stats* out);
+
 /* F-test critical values on their own (Sec. 3.2.2): out[t] = the
  * (1 - alpha_f) quantile of F(11, 12 (t J - 1)) for t = 1 .. t_max, FP64,
  * out[0] = 0.  out: device array of t_max + 1 doubles.  Enqueued on stream. */

@@ -1,6 +1,7 @@
 // ppm_api.cu -- the C ABI of libppm (declared in include/ppm.h): argument
 // checks, context lifecycle, the per-iteration sequence and state I/O.
 #include <math.h>
+#include <stddef.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -211,6 +212,15 @@ void free_ctx(ppm_ctx* c)
     ppm_sort_scratch_free(&c->sort);
     cudaFree(c->geom_dev); cudaFree(c->rmax); cudaFree(c->fc);
     cudaFree(c->counters); cudaFree(c->err_dev); cudaFree(c->feat);
+    if (c->copy_st) cudaStreamSynchronize(c->copy_st);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(c->hbuf[k]);
+        if (c->ev_copied[k]) cudaEventDestroy(c->ev_copied[k]);
+        if (c->ev_used[k]) cudaEventDestroy(c->ev_used[k]);
+        if (c->ev_stats[k]) cudaEventDestroy(c->ev_stats[k]);
+    }
+    if (c->hstats) cudaFreeHost(c->hstats);
+    if (c->copy_st) cudaStreamDestroy(c->copy_st);
     delete c;
 }
 
@@ -472,6 +482,148 @@ int ppm_stats(ppm_ctx* c, ppm_iter_stats* out)
     out->launches = c->launches_iter;
     out->gather_ms = -1.f;
     out->proposals = (int64_t)cnt[4];
+    return PPM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// bytes of one slot's photon arrays for n photons, each array 256-aligned
+struct HostLayout {
+    size_t pos, flux, nq, rho, wq, total;
+};
+
+HostLayout host_layout(int64_t n, int nch)
+{
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    HostLayout L;
+    L.pos = 0;
+    L.flux = L.pos + up((size_t)n * 3 * sizeof(float));
+    L.nq = L.flux + up((size_t)n * nch * sizeof(float));
+    L.rho = L.nq + up((size_t)n * sizeof(uint32_t));
+    L.wq = L.rho + up((size_t)n * 2 * sizeof(float));
+    L.total = L.wq + up((size_t)n * sizeof(uint32_t));
+    return L;
+}
+
+int host_feed_init(ppm_ctx* c)
+{
+    if (c->copy_st) return PPM_OK;
+    PPM_CUDA(cudaStreamCreateWithFlags(&c->copy_st, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+        PPM_CUDA(cudaEventCreateWithFlags(&c->ev_copied[k], cudaEventDisableTiming));
+        PPM_CUDA(cudaEventCreateWithFlags(&c->ev_used[k], cudaEventDisableTiming));
+        PPM_CUDA(cudaEventCreateWithFlags(&c->ev_stats[k], cudaEventDisableTiming));
+    }
+    void* hs = nullptr;
+    PPM_CUDA(cudaHostAlloc(&hs, 2 * sizeof(ppm_ctx::HostStats), cudaHostAllocDefault));
+    c->hstats = static_cast<ppm_ctx::HostStats*>(hs);
+    memset(c->hstats, 0, 2 * sizeof(ppm_ctx::HostStats));
+    return PPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ppm_iterate_host(ppm_ctx* c, const ppm_photons* ph, int32_t iter)
+{
+    PPM_ENTRY();
+    if (!c || !ph || ph->n < 0 || ph->n > 0xfffffff0ll || ph->J < 2) return PPM_EINVAL;
+    if (ph->channels != c->nch) return PPM_EINVAL;
+    if (ph->n > 0 && (!ph->pos || !ph->flux)) return PPM_EINVAL;
+    if (c->prm.vcm && ph->n > 0 && (!ph->rho || !ph->wq)) return PPM_EINVAL;
+    if (c->J != 0 && ph->J != c->J) return PPM_EINVAL;
+    if (iter != c->iter + 1) return PPM_ESTATE;
+    int rc = host_feed_init(c);
+    if (rc) return rc;
+    const int64_t n = ph->n;
+    const int k = c->host_slot;
+    if (n > c->hbuf_cap) {
+        // grow both slots: wait until neither is in use
+        PPM_CUDA(cudaStreamSynchronize(c->copy_st));
+        PPM_CUDA(cudaStreamSynchronize(c->stream));
+        const int64_t cap = n + n / 4 + 1024;
+        const HostLayout L = host_layout(cap, c->nch);
+        for (int s = 0; s < 2; ++s) {
+            cudaFree(c->hbuf[s]);
+            c->hbuf[s] = nullptr;
+        }
+        c->hbuf_cap = 0;
+        for (int s = 0; s < 2; ++s)
+            if (cudaMalloc(&c->hbuf[s], L.total) != cudaSuccess) { cudaGetLastError(); return PPM_ENOMEM; }
+        c->hbuf_cap = cap;
+    }
+    const HostLayout L = host_layout(c->hbuf_cap, c->nch);
+    unsigned char* base = c->hbuf[k];
+    ppm_photons d = *ph;
+    d.pos = reinterpret_cast<const float*>(base + L.pos);
+    d.flux = reinterpret_cast<const float*>(base + L.flux);
+    d.nq = ph->nq ? reinterpret_cast<const uint32_t*>(base + L.nq) : nullptr;
+    d.rho = ph->rho ? reinterpret_cast<const float*>(base + L.rho) : nullptr;
+    d.wq = ph->wq ? reinterpret_cast<const uint32_t*>(base + L.wq) : nullptr;
+    // the slot's previous contents were read by the build two iterations ago
+    PPM_CUDA(cudaStreamWaitEvent(c->copy_st, c->ev_used[k], 0));
+    if (n > 0) {
+        PPM_CUDA(cudaMemcpyAsync(base + L.pos, ph->pos, (size_t)n * 3 * sizeof(float),
+                                 cudaMemcpyHostToDevice, c->copy_st));
+        PPM_CUDA(cudaMemcpyAsync(base + L.flux, ph->flux, (size_t)n * c->nch * sizeof(float),
+                                 cudaMemcpyHostToDevice, c->copy_st));
+        if (ph->nq)
+            PPM_CUDA(cudaMemcpyAsync(base + L.nq, ph->nq, (size_t)n * sizeof(uint32_t),
+                                     cudaMemcpyHostToDevice, c->copy_st));
+        if (ph->rho)
+            PPM_CUDA(cudaMemcpyAsync(base + L.rho, ph->rho, (size_t)n * 2 * sizeof(float),
+                                     cudaMemcpyHostToDevice, c->copy_st));
+        if (ph->wq)
+            PPM_CUDA(cudaMemcpyAsync(base + L.wq, ph->wq, (size_t)n * sizeof(uint32_t),
+                                     cudaMemcpyHostToDevice, c->copy_st));
+    }
+    PPM_CUDA(cudaEventRecord(c->ev_copied[k], c->copy_st));
+    PPM_CUDA(cudaStreamWaitEvent(c->stream, c->ev_copied[k], 0));
+    rc = ppm_build_grid(c, &d);
+    if (rc) return rc;
+    PPM_CUDA(cudaEventRecord(c->ev_used[k], c->stream));
+    rc = ppm_gather_test_update(c, iter);
+    if (rc) return rc;
+    // this iteration's counters to page-locked memory
+    ppm_ctx::HostStats* hs = c->hstats + k;
+    PPM_CUDA(cudaMemcpyAsync(hs->cnt, c->counters, sizeof(hs->cnt), cudaMemcpyDeviceToHost, c->stream));
+    PPM_CUDA(cudaMemcpyAsync(&hs->r_max, c->rmax + c->rmax_cur, sizeof(float), cudaMemcpyDeviceToHost,
+                             c->stream));
+    PPM_CUDA(cudaMemcpyAsync(&hs->cell, reinterpret_cast<const char*>(c->geom_dev) + offsetof(GridGeom, h),
+                             sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    PPM_CUDA(cudaMemcpyAsync(&hs->err, c->err_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    PPM_CUDA(cudaEventRecord(c->ev_stats[k], c->stream));
+    c->host_iter[k] = iter;
+    c->host_launches[k] = c->launches_iter;
+    c->host_slot = k ^ 1;
+    return PPM_OK;
+}
+
+int ppm_stats_host(ppm_ctx* c, int32_t iter, ppm_iter_stats* out)
+{
+    PPM_ENTRY();
+    if (!c || !out) return PPM_EINVAL;
+    int k = -1;
+    for (int s = 0; s < 2; ++s)
+        if (c->hstats && iter > 0 && c->host_iter[s] == iter) k = s;
+    if (k < 0) return PPM_ESTATE;
+    PPM_CUDA(cudaEventSynchronize(c->ev_stats[k]));
+    const ppm_ctx::HostStats& hs = c->hstats[k];
+    memset(out, 0, sizeof(*out));
+    out->iter = iter;
+    out->flags = hs.err;
+    out->pairs = (int64_t)hs.cnt[0];
+    out->candidates = (int64_t)hs.cnt[1];
+    out->rejects = (int64_t)hs.cnt[2];
+    out->pairs_total = (int64_t)hs.cnt[3];
+    out->proposals = (int64_t)hs.cnt[4];
+    out->r_max = hs.r_max;
+    out->cell = hs.cell;
+    out->launches = c->host_launches[k];
+    out->gather_ms = -1.f;
     return PPM_OK;
 }
 

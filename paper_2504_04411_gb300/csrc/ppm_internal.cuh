@@ -179,6 +179,24 @@ struct ppm_ctx {
     const void* mlp = nullptr;        // caller-owned weight blob (device) or NULL
     float mlp_threshold = 0.5f;
     float mlp_max_shrink = 0.1f;
+    // host-fed iterations (ppm_iterate_host): two device photon buffers used
+    // in turn, filled on a private copy stream; counters land in pinned memory
+    cudaStream_t copy_st = nullptr;
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr};   // slot filled (copy stream)
+    cudaEvent_t ev_used[2] = {nullptr, nullptr};     // slot read by its build
+    cudaEvent_t ev_stats[2] = {nullptr, nullptr};    // counters copied out
+    unsigned char* hbuf[2] = {nullptr, nullptr};     // pos | flux | nq | rho | wq
+    int64_t hbuf_cap = 0;                            // photons per slot
+    struct HostStats {
+        unsigned long long cnt[5];
+        float r_max;
+        float cell;
+        int32_t err;
+        int32_t pad;
+    }* hstats = nullptr;                             // [2], page-locked
+    int32_t host_iter[2] = {0, 0};
+    int32_t host_launches[2] = {0, 0};
+    int host_slot = 0;
 };
 
 // ppm_grid.cu / ppm_gather.cu

@@ -63,7 +63,8 @@ EXPORTS = ("ppm_default_params", "ppm_create", "ppm_set_stream", "ppm_build_grid
            "ppm_batch_create", "ppm_batch_iterate", "ppm_batch_radiance",
            "ppm_batch_get_state", "ppm_batch_stats", "ppm_batch_graph_ready",
            "ppm_batch_destroy", "ppm_set_features", "ppm_get_features", "ppm_set_mlp",
-           "ppm_mlp_forward", "ppm_mlp_grad", "ppm_mlp_adam", "ppm_mlp_pack")
+           "ppm_mlp_forward", "ppm_mlp_grad", "ppm_mlp_adam", "ppm_mlp_pack",
+           "ppm_iterate_host", "ppm_stats_host")
 
 _lib = None
 
@@ -97,6 +98,10 @@ def load(path: str = LIB_PATH):
     L.ppm_set_iteration.argtypes = [c_p, ctypes.c_int32]
     L.ppm_stats.restype = ctypes.c_int
     L.ppm_stats.argtypes = [c_p, ctypes.POINTER(ppm_iter_stats)]
+    L.ppm_iterate_host.restype = ctypes.c_int
+    L.ppm_iterate_host.argtypes = [c_p, ctypes.POINTER(ppm_photons), ctypes.c_int32]
+    L.ppm_stats_host.restype = ctypes.c_int
+    L.ppm_stats_host.argtypes = [c_p, ctypes.c_int32, ctypes.POINTER(ppm_iter_stats)]
     L.ppm_f_critical.restype = ctypes.c_int
     L.ppm_f_critical.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_int32, c_p, c_p]
     L.ppm_sort_pairs.restype = ctypes.c_int
@@ -163,6 +168,16 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _host_ptr(t):
+    if t is None:
+        return None
+    if t.is_cuda:
+        raise ValueError("ppm_iterate_host takes host (CPU) tensors")
+    if not t.is_contiguous():
+        raise ValueError("libppm takes contiguous tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def _stream(stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
@@ -223,6 +238,23 @@ def ppm_set_iteration(ctx, it: int) -> None:
 def ppm_stats(ctx) -> ppm_iter_stats:
     s = ppm_iter_stats()
     _check("ppm_stats", load().ppm_stats(ctx, ctypes.byref(s)))
+    return s
+
+
+def ppm_iterate_host(ctx, it: int, pos, flux, J: int, nq=None, rho=None, wq=None) -> None:
+    """One iteration from host (CPU) tensors: copy, build, gather/test/update,
+    enqueued without waiting (pinned tensors overlap the copy with the
+    previous gather).  Keep the tensors alive and unchanged until
+    ppm_stats_host(ctx, it) has returned."""
+    channels = 3 if flux.dim() == 2 else 1
+    ph = ppm_photons(pos.shape[0], J, _host_ptr(pos), _host_ptr(flux), channels, 0,
+                     _host_ptr(nq), _host_ptr(rho), _host_ptr(wq))
+    _check("ppm_iterate_host", load().ppm_iterate_host(ctx, ctypes.byref(ph), it))
+
+
+def ppm_stats_host(ctx, it: int) -> ppm_iter_stats:
+    s = ppm_iter_stats()
+    _check("ppm_stats_host", load().ppm_stats_host(ctx, it, ctypes.byref(s)))
     return s
 
 
@@ -315,6 +347,19 @@ class Estimator:
                        wq=ph.wq if self.params.vcm else None)
         self.it += 1
         ppm_gather_test_update(self.ctx, self.it)
+
+    def step_host(self, ph, J: int | None = None) -> int:
+        """One iteration from host tensors (ppm_iterate_host); returns its
+        iteration number for ppm_stats_host."""
+        self.it += 1
+        try:
+            ppm_iterate_host(self.ctx, self.it, ph.pos, ph.flux, J if J is not None else ph.pos.shape[0],
+                             nq=ph.nq, rho=ph.rho if self.params.vcm else None,
+                             wq=ph.wq if self.params.vcm else None)
+        except Exception:
+            self.it -= 1
+            raise
+        return self.it
 
     def radiance(self) -> torch.Tensor:
         shape = (self.n,) if self.channels == 1 else (self.n, 3)
