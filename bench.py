@@ -61,9 +61,14 @@ def _src_hash(path):
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
 
 
-def _gather_sources_hash():
+# sources whose change invalidates a config's recorded DRAM traffic
+_TRAFFIC_SOURCES = {"frame": ("ppm_gather.cu", "ppm_gather_impl.cuh", "ppm_internal.cuh"),
+                    "batched": ("ppm_batch.cu", "ppm_gather_impl.cuh", "ppm_internal.cuh")}
+
+
+def _gather_sources_hash(config="frame"):
     h = hashlib.sha256()
-    for f in ("ppm_gather.cu", "ppm_gather_impl.cuh"):
+    for f in _TRAFFIC_SOURCES[config]:
         h.update(open(os.path.join(ROOT, "paper_2504_04411_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -76,7 +81,7 @@ def _profile_traffic(config):
     except Exception:
         return None
     ent = d.get(config)
-    if not ent or ent.get("src_sha") != _gather_sources_hash():
+    if not ent or config not in _TRAFFIC_SOURCES or ent.get("src_sha") != _gather_sources_hash(config):
         return None
     return ent.get("dram_bytes_per_launch")
 
@@ -424,7 +429,7 @@ def run_batched(args, rank, world, local, dist):
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     roof, other = roofline(gather_ms, sum(s.J for s in scenes), sum(s.nh for s in scenes), cand_last,
                            pairs_last, sm_count, "k_batch_gather")
-    roof["traffic"] = other["traffic"] = None
+    roof["traffic"] = other["traffic"] = _profile_traffic("batched")
     b.close()
     # the same problems and photons as separate contexts (the plain method)
     ests = []
