@@ -249,14 +249,17 @@ def main():
     return 0
 
 
-def _reduce(dist, seconds, count):
+def _reduce(dist, seconds, count, device="cuda"):
+    """Whole-job time and work over the ranks: the slowest rank's seconds
+    (MAX) and the sum of the units every rank processed.  device: where the
+    reduction tensors live (cuda for NCCL, cpu for gloo)."""
     if not dist:
         return seconds, float(count)
     import torch
     import torch.distributed as tdist
-    tm = torch.tensor([seconds], device="cuda", dtype=torch.float64)
+    tm = torch.tensor([seconds], device=device, dtype=torch.float64)
     tdist.all_reduce(tm, op=tdist.ReduceOp.MAX)
-    ts = torch.tensor([float(count)], device="cuda", dtype=torch.float64)
+    ts = torch.tensor([float(count)], device=device, dtype=torch.float64)
     tdist.all_reduce(ts, op=tdist.ReduceOp.SUM)
     return float(tm), float(ts)
 
