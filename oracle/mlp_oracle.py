@@ -2,12 +2,19 @@
 gradient (numpy).
 
 TEST INFRASTRUCTURE ONLY (imported by tests/), independent of the CUDA
-sources.  The network is 12 -> 64 -> 64 -> 2 with ReLU hidden layers; the
-weights given to the GPU are BF16, so the reference decodes the same BF16
-bits (exactly representable in FP64) and evaluates everything in FP64.
+sources.  The network is 12 -> 64 -> 64 -> 2 with ReLU hidden layers and
+this arithmetic: BF16 weights, FP32 biases, and the input of every layer
+(the features, h1, h2) rounded to BF16 (round to nearest even) -- the
+operand precision of the GPU's tensor-core products.  The reference decodes
+the same BF16 weight bits, applies the same rounding to the layer inputs
+and evaluates everything else in FP64.  The gradient treats the rounding
+as the identity (straight-through), as the GPU's training kernel does.
 Loss per sample: 0.5 m0 (o0 - y0)^2 + m1 BCE(o1, y1), BCE(z, y) =
 max(z, 0) - z y + log(1 + exp(-|z|)), times a common scale.
-Pinned in tests/test_mlp_oracle.py by central finite differences.
+Pinned in tests/test_mlp_oracle.py: the rounding against torch's bfloat16
+conversion; the unrounded network's gradient, and the straight-through
+gradient (rounding offsets frozen at the evaluation point), by central
+finite differences.
 """
 from __future__ import annotations
 
@@ -39,20 +46,38 @@ def from_blob(blob: bytes | np.ndarray) -> dict:
     return split(np.concatenate([weights, biases]))
 
 
-def forward(p: dict, X: np.ndarray):
+def bf16_round(x) -> np.ndarray:
+    """x rounded to the nearest BF16 value (ties to even) via float32, as
+    float64; no NaN or infinity inputs."""
+    u = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16 << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _layer_input_bf16(layer: int, v: np.ndarray) -> np.ndarray:
+    return bf16_round(v)
+
+
+def forward(p: dict, X: np.ndarray, act=_layer_input_bf16):
+    """Outputs and intermediates.  act(layer, v) maps the input v of layer
+    0, 1, 2 (the features, h1, h2) to what the layer multiplies: BF16
+    rounding by default (the network's definition); identity for the exact
+    real-valued network."""
     X = np.asarray(X, np.float64)
-    z1 = X @ p["W1"].T + p["b1"]
-    h1 = np.maximum(z1, 0.0)
+    xb = act(0, X)
+    z1 = xb @ p["W1"].T + p["b1"]
+    h1 = act(1, np.maximum(z1, 0.0))
     z2 = h1 @ p["W2"].T + p["b2"]
-    h2 = np.maximum(z2, 0.0)
+    h2 = act(2, np.maximum(z2, 0.0))
     out = h2 @ p["W3"].T + p["b3"]
-    return out, (X, z1, h1, z2, h2)
+    return out, (xb, z1, h1, z2, h2)
 
 
-def loss_and_grad(p: dict, X, Y, M, scale: float):
+def loss_and_grad(p: dict, X, Y, M, scale: float, act=_layer_input_bf16):
     """Loss and its gradient w.r.t. every parameter, flattened in the order
-    W1, W2, W3, b1, b2, b3 (the master-parameter order)."""
-    out, (X, z1, h1, z2, h2) = forward(p, X)
+    W1, W2, W3, b1, b2, b3 (the master-parameter order).  act as in
+    forward; its effect is differentiated as the identity."""
+    out, (xb, z1, h1, z2, h2) = forward(p, X, act)
     Y = np.asarray(Y, np.float64)
     M = np.asarray(M, np.float64)
     e = out[:, 0] - Y[:, 0]
@@ -67,11 +92,11 @@ def loss_and_grad(p: dict, X, Y, M, scale: float):
     dW2 = dh2.T @ h1
     db2 = dh2.sum(0)
     dh1 = (dh2 @ p["W2"]) * (z1 > 0)
-    dW1 = dh1.T @ X
+    dW1 = dh1.T @ xb
     db1 = dh1.sum(0)
     grad = np.concatenate([dW1.ravel(), dW2.ravel(), dW3.ravel(), db1, db2, db3])
     return loss, grad
 
 
-def loss_only(flat: np.ndarray, X, Y, M, scale: float) -> float:
-    return loss_and_grad(split(flat), X, Y, M, scale)[0]
+def loss_only(flat: np.ndarray, X, Y, M, scale: float, act=_layer_input_bf16) -> float:
+    return loss_and_grad(split(flat), X, Y, M, scale, act)[0]

@@ -1,6 +1,7 @@
 // ppm_mlp.cu -- the learned radius proposer: a 12 -> 64 -> 64 -> 2 MLP (ReLU
-// hidden layers) with BF16 weights and FP32 biases, activations and
-// accumulation.
+// hidden layers).  Arithmetic: BF16 weights, FP32 biases, every layer's
+// input (features, h1, h2) rounded to BF16 (round to nearest even from the
+// FP32 value), FP32 accumulation.
 //
 // Inputs: the 12 window features the gather's epilogue writes per hit
 // point (ppm_gather_impl.cuh).  Outputs: o0 = predicted log(r_final / r),
@@ -8,17 +9,23 @@
 // Training data comes from runs of the plain method; the loss is
 // 0.5 (o0 - y0)^2 + BCE(o1, y1) with per-sample weights, minimized with Adam
 // (Kingma & Ba 2015) on FP32 master weights whose BF16 copies drive the
-// forward passes.  After the F-test update of every iteration the proposer
+// forward passes (the BF16 rounding of the activations is differentiated
+// as the identity).  After the F-test update of every iteration the proposer
 // shrinks the radius of a hit point the test did not just reject when the
 // network calls it doomed: r <- max(r max(exp(o0), min_ratio), bound); the
 // window is cleared as on a rejection.  The F-test still runs every
 // iteration on whatever radius a hit point has: it stays the judge.
 //
-// The network is tiny (4,992 MACs per sample): one thread per sample on the
-// FP32 pipes, weights broadcast from shared memory.  Gradients are reduced
-// per 128-sample tile from shared-memory activations stored feature-major
-// with a row stride of 129 words, so the lanes of a warp always hit
-// distinct banks.
+// Inference (k_mlp_forward, k_mlp_propose) runs on the tensor cores: a warp
+// takes 16 samples through all three layers with mma.sync m16n8k16 BF16
+// products (8 + 32 + 4 per tile).  The FP32 accumulator fragment of one
+// layer, after bias, ReLU and BF16 packing, is exactly the A fragment of the
+// next, so activations never leave registers; weights sit in shared memory
+// with padded rows (B-fragment loads hit 32 distinct banks).  Training
+// (k_mlp_grad) is one thread per sample on the FP32 pipes: it needs the
+// activations of a 128-sample tile in shared memory for the weight
+// gradients anyway, stored feature-major with a row stride of 129 words so
+// the lanes of a warp always hit distinct banks.
 #include <cuda_bf16.h>
 
 #include "ppm_internal.cuh"
@@ -54,47 +61,157 @@ __device__ __forceinline__ void load_weights(MlpSmem& w, const uint8_t* blob)
     __syncthreads();
 }
 
-__device__ __forceinline__ void mlp_forward(const MlpSmem& w, const float (&x)[kIn], float& o0, float& o1)
+// ---- tensor-core inference --------------------------------------------------
+// B fragments of m16n8k16 (k x n, column-major) are pairs W[n][k], W[n][k+1]
+// of the row-major [out][in] weights: one 32-bit shared load each.  Row
+// strides of 12 words (W1: 12 inputs + 4 zero, + pad) and 36 words (W2, W3)
+// put the 8 rows x 4 words a warp loads on 32 distinct banks.
+constexpr int kLdW1 = 24;   // bf16 per W1 row
+constexpr int kLdW2 = 72;   // bf16 per W2 / W3 row
+
+struct __align__(16) TcSmem {
+    __nv_bfloat16 W1[kH][kLdW1];     // k >= 12 zero
+    __nv_bfloat16 W2[kH][kLdW2];
+    __nv_bfloat16 W3[8][kLdW2];      // rows >= 2 zero (the output tile is 8 wide)
+    float b1[kH], b2[kH], b3[kOut];
+};
+
+__device__ void load_tc_weights(TcSmem& w, const uint8_t* blob)
 {
-    float h1[kH];
-#pragma unroll
-    for (int k = 0; k < kH; ++k) {
-        float z = w.b1[k];
-#pragma unroll
-        for (int i = 0; i < kIn; ++i) z = fmaf(w.W1[k * kIn + i], x[i], z);
-        h1[k] = fmaxf(z, 0.f);
+    const __nv_bfloat16* wb = reinterpret_cast<const __nv_bfloat16*>(blob);
+    const float* bb = reinterpret_cast<const float*>(blob + kOffB);
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+    for (int e = threadIdx.x; e < kH * kLdW1; e += blockDim.x) {
+        const int n = e / kLdW1, k = e % kLdW1;
+        w.W1[n][k] = k < kIn ? wb[n * kIn + k] : zero;
     }
-    o0 = w.b3[0];
-    o1 = w.b3[1];
-#pragma unroll 4
-    for (int j = 0; j < kH; ++j) {
-        float z = w.b2[j];
-#pragma unroll
-        for (int k = 0; k < kH; ++k) z = fmaf(w.W2[j * kH + k], h1[k], z);
-        z = fmaxf(z, 0.f);
-        o0 = fmaf(w.W3[j], z, o0);
-        o1 = fmaf(w.W3[kH + j], z, o1);
+    for (int e = threadIdx.x; e < kH * kLdW2; e += blockDim.x) {
+        const int n = e / kLdW2, k = e % kLdW2;
+        w.W2[n][k] = k < kH ? wb[kW1 + n * kH + k] : zero;
     }
+    for (int e = threadIdx.x; e < 8 * kLdW2; e += blockDim.x) {
+        const int n = e / kLdW2, k = e % kLdW2;
+        w.W3[n][k] = (n < kOut && k < kH) ? wb[kW1 + kW2 + n * kH + k] : zero;
+    }
+    for (int e = threadIdx.x; e < kH + kH + kOut; e += blockDim.x) {
+        const float v = bb[e];
+        if (e < kH) w.b1[e] = v;
+        else if (e < 2 * kH) w.b2[e - kH] = v;
+        else w.b3[e - 2 * kH] = v;
+    }
+    __syncthreads();
 }
 
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ uint32_t lds_u32(const __nv_bfloat16* p)
+{
+    return *reinterpret_cast<const uint32_t*>(p);
+}
+
+// c += A (16 x 16, row-major BF16) * B (16 x 8, column-major BF16), FP32
+__device__ __forceinline__ void mma_bf16_16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// One hidden layer's 8 output tiles (64 units) -> the next layer's A
+// fragments: tile j holds units 8j..8j+7, i.e. half j % 2 of k-step j / 2.
+// c[0], c[1]: row g, units 8j + 2t, +1; c[2], c[3]: row g + 8.
+__device__ __forceinline__ void to_next_a(uint32_t (&A)[4][4], int j, const float (&c)[4], float bA, float bB)
+{
+    const uint32_t lo = pack_bf16x2(fmaxf(c[0] + bA, 0.f), fmaxf(c[1] + bB, 0.f));
+    const uint32_t hi = pack_bf16x2(fmaxf(c[2] + bA, 0.f), fmaxf(c[3] + bB, 0.f));
+    if (j % 2 == 0) { A[j / 2][0] = lo; A[j / 2][1] = hi; }
+    else            { A[j / 2][2] = lo; A[j / 2][3] = hi; }
+}
+
+// 16 samples through the network.  xa: this lane's layer-1 A fragment
+// (rows g = lane / 4 and g + 8 of the tile, features 2t, 2t+1 and 2t+8,
+// 2t+9 with t = lane % 4, BF16).  On return, lanes with t == 0 hold
+// o[0], o[1] = (o0, o1) of row g and o[2], o[3] of row g + 8.
+__device__ __forceinline__ void mlp_tile(const TcSmem& w, const uint32_t (&xa)[4], float (&o)[4])
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    uint32_t A2[4][4], A3[4][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_bf16_16816(c, xa, lds_u32(&w.W1[8 * j + g][2 * t]), lds_u32(&w.W1[8 * j + g][2 * t + 8]));
+        to_next_a(A2, j, c, w.b1[8 * j + 2 * t], w.b1[8 * j + 2 * t + 1]);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            mma_bf16_16816(c, A2[q], lds_u32(&w.W2[8 * j + g][16 * q + 2 * t]),
+                           lds_u32(&w.W2[8 * j + g][16 * q + 2 * t + 8]));
+        to_next_a(A3, j, c, w.b2[8 * j + 2 * t], w.b2[8 * j + 2 * t + 1]);
+    }
+    float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        mma_bf16_16816(c, A3[q], lds_u32(&w.W3[g][16 * q + 2 * t]), lds_u32(&w.W3[g][16 * q + 2 * t + 8]));
+    o[0] = c[0] + w.b3[0];
+    o[1] = c[1] + w.b3[1];
+    o[2] = c[2] + w.b3[0];
+    o[3] = c[3] + w.b3[1];
+}
+
+// layer-1 A fragment of the tile whose row g is sample s0 + g; feature f of
+// sample s is x(s, f); samples >= n and features >= 12 are zero
+template <typename XF>
+__device__ __forceinline__ void load_x_fragment(uint32_t (&xa)[4], int64_t s0, int64_t n, XF x)
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int64_t sA = s0 + g, sB = s0 + g + 8;
+    const int f0 = 2 * t, f1 = 2 * t + 8;
+    auto val = [&](int64_t s, int f) { return (s < n && f < kIn) ? x(s, f) : 0.f; };
+    xa[0] = pack_bf16x2(val(sA, f0), val(sA, f0 + 1));
+    xa[1] = pack_bf16x2(val(sB, f0), val(sB, f0 + 1));
+    xa[2] = pack_bf16x2(val(sA, f1), val(sA, f1 + 1));
+    xa[3] = pack_bf16x2(val(sB, f1), val(sB, f1 + 1));
+}
+
+constexpr int kTcWarps = 4;
+
+__global__ void __launch_bounds__(32 * kTcWarps)
 k_mlp_forward(const uint8_t* __restrict__ blob, const float* __restrict__ X, int64_t n,
               float* __restrict__ Y)
 {
-    __shared__ MlpSmem w;
-    load_weights(w, blob);
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    float x[kIn];
-#pragma unroll
-    for (int i = 0; i < kIn; ++i) x[i] = X[s * kIn + i];
-    float o0, o1;
-    mlp_forward(w, x, o0, o1);
-    Y[2 * s] = o0;
-    Y[2 * s + 1] = o1;
+    __shared__ TcSmem w;
+    load_tc_weights(w, blob);
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int64_t tiles = (n + 15) / 16;
+    for (int64_t tile = (int64_t)blockIdx.x * kTcWarps + (threadIdx.x >> 5); tile < tiles;
+         tile += (int64_t)gridDim.x * kTcWarps) {
+        const int64_t s0 = tile * 16;
+        uint32_t xa[4];
+        load_x_fragment(xa, s0, n, [&](int64_t s, int f) { return X[s * kIn + f]; });
+        float o[4];
+        mlp_tile(w, xa, o);
+        if (t == 0) {
+            if (s0 + g < n) { Y[2 * (s0 + g)] = o[0]; Y[2 * (s0 + g) + 1] = o[1]; }
+            if (s0 + g + 8 < n) { Y[2 * (s0 + g + 8)] = o[2]; Y[2 * (s0 + g + 8) + 1] = o[3]; }
+        }
+    }
 }
 
 // ---- gradient of one 128-sample tile ----------------------------------------
+__device__ __forceinline__ float bf16_round(float v)
+{
+    return __bfloat162float(__float2bfloat16_rn(v));
+}
+
 constexpr int kTile = 128;
 constexpr int kLd = kTile + 1;        // row stride: lanes hit distinct banks
 
@@ -123,20 +240,20 @@ k_mlp_grad(const uint8_t* __restrict__ blob, const float* __restrict__ X, const 
     // forward, keeping the activations
     float x[kIn];
 #pragma unroll
-    for (int i = 0; i < kIn; ++i) { x[i] = live ? X[gs * kIn + i] : 0.f; sm.x[i][s] = x[i]; }
+    for (int i = 0; i < kIn; ++i) { x[i] = bf16_round(live ? X[gs * kIn + i] : 0.f); sm.x[i][s] = x[i]; }
 #pragma unroll 4
     for (int k = 0; k < kH; ++k) {
         float z = sm.w.b1[k];
 #pragma unroll
         for (int i = 0; i < kIn; ++i) z = fmaf(sm.w.W1[k * kIn + i], x[i], z);
-        sm.h1[k][s] = fmaxf(z, 0.f);
+        sm.h1[k][s] = bf16_round(fmaxf(z, 0.f));
     }
     float o0 = sm.w.b3[0], o1 = sm.w.b3[1];
     for (int j = 0; j < kH; ++j) {
         float z = sm.w.b2[j];
 #pragma unroll 8
         for (int k = 0; k < kH; ++k) z = fmaf(sm.w.W2[j * kH + k], sm.h1[k][s], z);
-        z = fmaxf(z, 0.f);
+        z = bf16_round(fmaxf(z, 0.f));
         sm.h2[j][s] = z;
         o0 = fmaf(sm.w.W3[j], z, o0);
         o1 = fmaf(sm.w.W3[kH + j], z, o1);
@@ -228,38 +345,50 @@ __global__ void k_mlp_pack(const float* __restrict__ master, uint8_t* __restrict
 }
 
 // after the F-test update: shrink the doomed radii the test did not reject
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ unsigned long long propose_one(int64_t h, int64_t nh, int ntc, float o0, float o1,
+                                                          float* r, int32_t* t, uint32_t* cnt, float* S,
+                                                          float* Q, float bound, float thr_logit,
+                                                          float min_ratio)
+{
+    if (h >= nh || t[h] <= 0) return 0;            // t == 0: the test rejected it just now
+    if (!(o1 > thr_logit && o0 < 0.f)) return 0;
+    const float rr = r[h];
+    const float rn = fmaxf(__fmul_rn(rr, fmaxf(expf(o0), min_ratio)), bound);
+    if (!(rn < rr)) return 0;
+    r[h] = rn;
+    t[h] = 0;
+#pragma unroll
+    for (int g = 0; g < PPM_NG; ++g) cnt[g * nh + h] = 0u;
+    for (int c = 0; c < ntc; ++c)
+#pragma unroll
+        for (int g = 0; g < PPM_NG; ++g) {
+            S[((int64_t)c * PPM_NG + g) * nh + h] = 0.f;
+            Q[((int64_t)c * PPM_NG + g) * nh + h] = 0.f;
+        }
+    return 1;
+}
+
+__global__ void __launch_bounds__(32 * kTcWarps)
 k_mlp_propose(int64_t nh, int ntc, const uint8_t* __restrict__ blob, const float* __restrict__ feat,
               float* __restrict__ r, int32_t* __restrict__ t, uint32_t* __restrict__ cnt,
               float* __restrict__ S, float* __restrict__ Q, float bound, float thr_logit,
               float min_ratio, unsigned long long* __restrict__ proposals)
 {
-    __shared__ MlpSmem w;
-    load_weights(w, blob);
-    const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ TcSmem w;
+    load_tc_weights(w, blob);
+    const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+    const int64_t tiles = (nh + 15) / 16;
     unsigned long long shrunk = 0;
-    if (h < nh && t[h] > 0) {                       // t == 0: the test rejected it just now
-        float x[kIn];
-#pragma unroll
-        for (int q = 0; q < kIn; ++q) x[q] = feat[(int64_t)q * nh + h];
-        float o0, o1;
-        mlp_forward(w, x, o0, o1);
-        if (o1 > thr_logit && o0 < 0.f) {
-            const float rr = r[h];
-            const float rn = fmaxf(__fmul_rn(rr, fmaxf(expf(o0), min_ratio)), bound);
-            if (rn < rr) {
-                r[h] = rn;
-                t[h] = 0;
-#pragma unroll
-                for (int g = 0; g < PPM_NG; ++g) cnt[g * nh + h] = 0u;
-                for (int c = 0; c < ntc; ++c)
-#pragma unroll
-                    for (int g = 0; g < PPM_NG; ++g) {
-                        S[((int64_t)c * PPM_NG + g) * nh + h] = 0.f;
-                        Q[((int64_t)c * PPM_NG + g) * nh + h] = 0.f;
-                    }
-                shrunk = 1;
-            }
+    for (int64_t tile = (int64_t)blockIdx.x * kTcWarps + (threadIdx.x >> 5); tile < tiles;
+         tile += (int64_t)gridDim.x * kTcWarps) {
+        const int64_t s0 = tile * 16;
+        uint32_t xa[4];
+        load_x_fragment(xa, s0, nh, [&](int64_t s, int f) { return feat[(int64_t)f * nh + s]; });
+        float o[4];
+        mlp_tile(w, xa, o);
+        if (tq == 0) {
+            shrunk += propose_one(s0 + g, nh, ntc, o[0], o[1], r, t, cnt, S, Q, bound, thr_logit, min_ratio);
+            shrunk += propose_one(s0 + g + 8, nh, ntc, o[2], o[3], r, t, cnt, S, Q, bound, thr_logit, min_ratio);
         }
     }
 #pragma unroll
@@ -277,6 +406,15 @@ __global__ void k_features_out(int64_t nh, const float* __restrict__ feat, const
     for (int q = 0; q < kIn; ++q) out[o * kIn + q] = feat[(int64_t)q * nh + h];
 }
 
+// blocks for n samples: one 16-sample tile per warp, at most 4096 blocks
+// (the kernels loop over the tiles)
+unsigned tc_grid(int64_t n)
+{
+    const int64_t tiles = (n + 15) / 16;
+    const int64_t blocks = (tiles + kTcWarps - 1) / kTcWarps;
+    return (unsigned)(blocks < 1 ? 1 : (blocks > 4096 ? 4096 : blocks));
+}
+
 }  // namespace
 
 int ppm_mlp_propose_launch(ppm_ctx* c, float bound)
@@ -284,7 +422,7 @@ int ppm_mlp_propose_launch(ppm_ctx* c, float bound)
     if (!c->mlp || c->nh == 0) return PPM_OK;
     const float thr = c->mlp_threshold;
     const float thr_logit = logf(thr / (1.f - thr));
-    k_mlp_propose<<<(unsigned)((c->nh + 255) / 256), 256, 0, c->stream>>>(
+    k_mlp_propose<<<tc_grid(c->nh), 32 * kTcWarps, 0, c->stream>>>(
         c->nh, c->ntc, (const uint8_t*)c->mlp, c->feat, c->r, c->t, c->cnt, c->S, c->Q, bound,
         thr_logit, c->mlp_max_shrink, c->counters + 4);
     PPM_LAUNCH_CHECK();
@@ -348,7 +486,7 @@ int ppm_mlp_forward(const void* blob, const float* X, int64_t n, float* Y, void*
     PPM_ENTRY();
     if (!blob || n < 0 || (n > 0 && (!X || !Y))) return PPM_EINVAL;
     if (n == 0) return PPM_OK;
-    k_mlp_forward<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>((const uint8_t*)blob, X, n, Y);
+    k_mlp_forward<<<tc_grid(n), 32 * kTcWarps, 0, (cudaStream_t)stream>>>((const uint8_t*)blob, X, n, Y);
     PPM_LAUNCH_CHECK();
     return PPM_OK;
 }
