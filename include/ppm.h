@@ -223,8 +223,10 @@ int ppm_sort_pairs(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* k
                    uint32_t* vals_out, int64_t n, int32_t bits, void* stream);
 
 /* ---- learned radius proposer (not in the paper) ----------------------------
- * A 12 -> 64 -> 64 -> 2 MLP with ReLU hidden layers, BF16 weights, FP32
- * biases, activations and accumulation.  Input: 12 features of the window a
+ * A 12 -> 64 -> 64 -> 2 MLP with ReLU hidden layers: BF16 weights, FP32
+ * biases and accumulation, every layer's input (features, h1, h2) rounded
+ * to BF16 (nearest even); inference runs on the tensor cores.  The
+ * gradient treats that rounding as the identity.  Input: 12 features of the window a
  * hit point's F-test just used -- log(1+C), log(1+t'), log i, r/r0,
  * log(r/r0), log(1+F), F/F_c, max_g S_g/S, min_g S_g/S, fraction of empty
  * groups, coefficient of variation of the group sums, max_g c_g/C (C, S:
