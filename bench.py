@@ -43,11 +43,18 @@ UNIT = "pairs/s"
 # algorithmic bytes of one gather launch (k_gather_update), per unit
 GATHER_BYTES_PER_PHOTON = 16 + 4          # sorted record + normal word, read once
 GATHER_BYTES_PER_HIT = 48 + 4 + 4 + 8 + 144 + (4 + 4 + 8 + 4 + 144)
+# VCM+ with RGB flux: three 16-byte records per photon (x y z psi | R G B
+# rho_vm_l | normal, direction, rho_vc_l); RGB tau (24 B) per hit point
+GATHER_BYTES_PER_PHOTON_VCM = 16 + 16 + 16
+GATHER_BYTES_PER_HIT_VCM = 48 + 4 + 4 + 24 + 144 + (4 + 4 + 24 + 4 + 144)
 # static record read; r, t, tau and the window (12 x count, S, Q) read;
 # r, t, tau, F and the window written
 # algorithmic FP32/INT operations of the canonical per-pair sequence
 OPS_PER_CANDIDATE = 7     # 3 sub, 1 mul + 2 fma (d^2), 1 compare
 OPS_PER_PAIR = 28         # normal dp4a+cmp 2, map 6, rho^2 2, ring 2, sector 9, group 1, accumulate 4, flux 2
+# + merge weight (cosine dp4a, scale, 2 fma/add, R_VC/eta, reciprocal: 8),
+# weighted psi 1, weighted RGB flux 3, compensated RGB sums 12
+OPS_PER_PAIR_VCM = OPS_PER_PAIR + 8 + 1 + 3 + 12
 
 
 def _peaks():
@@ -63,6 +70,7 @@ def _src_hash(path):
 
 # sources whose change invalidates a config's recorded DRAM traffic
 _TRAFFIC_SOURCES = {"frame": ("ppm_gather.cu", "ppm_gather_impl.cuh", "ppm_internal.cuh"),
+                    "vcm": ("ppm_gather.cu", "ppm_gather_impl.cuh", "ppm_internal.cuh"),
                     "batched": ("ppm_batch.cu", "ppm_gather_impl.cuh", "ppm_internal.cuh")}
 
 
@@ -135,9 +143,10 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- oracle --
-def oracle_sample(scene, batches_np, hp_np, n_hits, seed=0):
+def oracle_sample(scene, batches_np, hp_np, n_hits, seed=0, **kw):
     """Run the CPU oracle (as it stands) over one iteration for a random
-    subset of hit points; returns (pairs, seconds)."""
+    subset of hit points; returns (pairs, seconds).  kw: method options of
+    oracle.run (vcm, k)."""
     import numpy as np
 
     from oracle import oracle as O
@@ -145,18 +154,18 @@ def oracle_sample(scene, batches_np, hp_np, n_hits, seed=0):
     idx = np.sort(rng.choice(hp_np["pos"].shape[0], n_hits, replace=False))
     sub = {k: v[idx] for k, v in hp_np.items()}
     t0 = time.perf_counter()
-    res = O.run(sub, batches_np, scene.r0, 1, outputs=True)
+    res = O.run(sub, batches_np, scene.r0, 1, outputs=True, **kw)
     dt = time.perf_counter() - t0
     return int(res.pairs.sum()), dt
 
 
-def cpu_baseline(scene, hp_np, ph_np, budget_s=12.0):
+def cpu_baseline(scene, hp_np, ph_np, budget_s=12.0, **kw):
     threads = os.cpu_count() or 1
     os.environ.setdefault("OMP_NUM_THREADS", str(threads))
     probe = 128
-    _, dt = oracle_sample(scene, ph_np, hp_np, probe, seed=1)
+    _, dt = oracle_sample(scene, ph_np, hp_np, probe, seed=1, **kw)
     n = int(min(hp_np["pos"].shape[0], max(probe, probe * budget_s / max(dt, 1e-3))))
-    pairs, dt = oracle_sample(scene, ph_np, hp_np, n, seed=2)
+    pairs, dt = oracle_sample(scene, ph_np, hp_np, n, seed=2, **kw)
     return {"value": pairs / dt, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", threads)),
             "kind": "oracle",
             "sample": f"{n} random hit points of the workload x 1 iteration of {ph_np['pos'].shape[1]} "
@@ -170,7 +179,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="frame", choices=["frame", "tiny", "batched", "learned"])
+    ap.add_argument("--config", default="frame", choices=["frame", "tiny", "batched", "learned", "vcm"])
     ap.add_argument("--mapping", type=int, default=None, help="skip the autotuner: traversal")
     ap.add_argument("--cell-factor", type=float, default=None, help="skip the autotuner: cell factor")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -178,7 +187,7 @@ def parse():
     ap.add_argument("--no-flush", action="store_true")
     a = ap.parse_args()
     if a.steps is None:
-        a.steps = 16 if a.config == "batched" else (64 if a.config == "learned" else 64 - a.warmup)
+        a.steps = 16 if a.config in ("batched", "vcm") else (64 if a.config == "learned" else 64 - a.warmup)
     return a
 
 
@@ -188,6 +197,13 @@ def make_scene(config, rank):
         sc = synth.PlaneScene(nside=64, J=100_000, r0=0.02, step=True, seed=synth.SEED_BASE + 1000 * rank)
         desc = {"workload": "plain, tiny: 64x64 hit points on z=0, 100k photons/iter, step edge, r0=0.02",
                 "hit_points": 4096, "photons_per_iter": 100_000, "r0": 0.02}
+    elif config == "vcm":
+        sc = synth.BoxScene(nh=3840 * 2160, J=16_000_000, r0=0.0026, rgb=True, vcm=True,
+                            seed=synth.SEED_BASE + 5 + 1000 * rank)
+        desc = {"workload": "VCM+ merge, 4K: 3840x2160 hit points on 3 faces of the unit box, 16M light "
+                            "vertices/iter with RGB flux (lobe tints), log-normal pdf ratios, cosine "
+                            "directions; r0=0.0026 (0.3% of the bounding radius), k=0.9, luminance test",
+                "hit_points": sc.nh, "photons_per_iter": sc.J, "r0": sc.r0}
     else:
         sc = synth.BoxScene(seed=synth.SEED_BASE + 1 + 1000 * rank)
         desc = {"workload": "plain, frame-sized: 1920x1080 hit points on 3 faces of the unit box, "
@@ -196,13 +212,16 @@ def make_scene(config, rank):
     return sc, desc
 
 
-def roofline(g_ms, photons, hits, candidates, pairs, sm_count, kernel):
+def roofline(g_ms, photons, hits, candidates, pairs, sm_count, kernel, vcm=False):
     peaks = _peaks()
     g_s = g_ms / 1e3
-    bytes_launch = photons * GATHER_BYTES_PER_PHOTON + hits * GATHER_BYTES_PER_HIT
+    if vcm:
+        bytes_launch = photons * GATHER_BYTES_PER_PHOTON_VCM + hits * GATHER_BYTES_PER_HIT_VCM
+    else:
+        bytes_launch = photons * GATHER_BYTES_PER_PHOTON + hits * GATHER_BYTES_PER_HIT
     hbm_achieved = bytes_launch / g_s / 1e9
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    ops_launch = candidates * OPS_PER_CANDIDATE + pairs * OPS_PER_PAIR
+    ops_launch = candidates * OPS_PER_CANDIDATE + pairs * (OPS_PER_PAIR_VCM if vcm else OPS_PER_PAIR)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     alu_peak = sm_count * 128 * sm_mhz * 1e6 / 1e12
     alu_achieved = ops_launch / g_s / 1e12
@@ -273,12 +292,15 @@ def run_single(args, rank, world, local, dist):
     hp = sc.hitpoints("cuda")
     batches = [sc.photons(i, "cuda") for i in range(1, W + K + 1)]
     torch.cuda.synchronize()
+    vcm = args.config == "vcm"
+    params = ppm.ppm_default_params()
+    if vcm:
+        params.channels, params.vcm, params.k = 3, 1, 0.9
     # autotuner: traversal and cell factor (before the timed region)
     if args.mapping is not None and args.cell_factor is not None:
         tuned = {"mapping": args.mapping, "cell_factor": args.cell_factor, "key": "given"}
     else:
-        tuned = autotune.tune(hp, batches[:3], sc.r0)
-    params = ppm.ppm_default_params()
+        tuned = autotune.tune(hp, batches[:3], sc.r0, params=params)
     params.mapping, params.cell_factor = tuned["mapping"], tuned["cell_factor"]
     flush = None if args.no_flush else torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -305,7 +327,8 @@ def run_single(args, rank, world, local, dist):
         a, b, c = ev[i]
         ph = batches[W + i]
         a.record(stream)
-        ppm.ppm_build_grid(est.ctx, ph.pos, ph.flux, ph.pos.shape[0], nq=ph.nq)
+        ppm.ppm_build_grid(est.ctx, ph.pos, ph.flux, ph.pos.shape[0], nq=ph.nq,
+                           rho=ph.rho if vcm else None, wq=ph.wq if vcm else None)
         b.record(stream)
         est.it += 1
         ppm.ppm_gather_test_update(est.ctx, est.it)
@@ -324,7 +347,7 @@ def run_single(args, rank, world, local, dist):
     value = all_pairs / total_s
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     roof, other = roofline(statistics.mean(gather_ms), sc.J, hp.n, st.candidates, st.pairs, sm_count,
-                           "k_gather_update")
+                           "k_gather_update", vcm=vcm)
     roof["traffic"] = other["traffic"] = _profile_traffic(args.config)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -341,35 +364,48 @@ def run_single(args, rank, world, local, dist):
             "candidates_last_iter": st.candidates, "pairs_last_iter": st.pairs,
             "rejects_last_iter": st.rejects}
     if not args.no_e2e:
-        e2e = run_e2e(est, batches, W, K)
+        e2e = run_e2e(est, sc, W + K + 1, K, max_steps=8 if vcm else None)
         secs, cnt = _reduce(dist, e2e["seconds"], e2e["pairs"])
         line["e2e"] = {"value": cnt / secs, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
-                       "d2h_bytes_per_step": e2e["d2h"]}
+                       "d2h_bytes_per_step": e2e["d2h"], "steps": e2e["steps"],
+                       "inputs": "fresh photons per step (iterations after the timed ones), page-locked"}
     est.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         hp_np = hp.numpy()
         ph_np = synth.stack_numpy([batches[W]])
         del batches
-        line["cpu_baseline"] = cpu_baseline(sc, hp_np, ph_np)
+        line["cpu_baseline"] = cpu_baseline(sc, hp_np, ph_np, **({"vcm": True, "k": 0.9} if vcm else {}))
     return line
 
 
-def run_e2e(est, batches, W, K):
-    """The same iterations through the public C API with host-resident
-    inputs: each step hands its photons, in page-locked host memory, to
-    ppm_iterate_host (copy to the device, grid build, gather/test/update;
-    the copy overlaps the previous step's gather) and reads the previous
-    step's counters back with ppm_stats_host; the last step's counters are
-    read after the loop, inside the timed region."""
+def _pinned(t):
+    return None if t is None else t.cpu().pin_memory()
+
+
+def run_e2e(est, sc, first_iter, K, max_steps=None):
+    """The same method through the public C API with host-resident inputs:
+    each step hands fresh photons (those of iterations first_iter,
+    first_iter + 1, ...; made on the device and copied to page-locked host
+    memory before the timed region) to ppm_iterate_host (copy to the device,
+    grid build, gather/test/update; the copy overlaps the previous step's
+    gather) and reads the previous step's counters back with
+    ppm_stats_host; the last step's counters are read after the loop, inside
+    the timed region.  Photons are never fed twice: repeated photons would
+    inflate the F statistic and shrink every radius."""
     import torch
 
     from paper_2504_04411_gb300 import ppm
+    vcm = bool(est.params.vcm)
+    K = K if max_steps is None else min(K, max_steps)
     host = []
     for i in range(K):
-        ph = batches[W + i]
-        host.append(dataclasses.replace(ph, pos=ph.pos.cpu().pin_memory(), flux=ph.flux.cpu().pin_memory(),
-                                        nq=ph.nq.cpu().pin_memory()))
-    h2d = sum(t.numel() * t.element_size() for t in (host[0].pos, host[0].flux, host[0].nq))
+        ph = sc.photons(first_iter + i, "cuda")
+        host.append(dataclasses.replace(ph, pos=_pinned(ph.pos), flux=_pinned(ph.flux), nq=_pinned(ph.nq),
+                                        rho=_pinned(ph.rho) if vcm else None,
+                                        wq=_pinned(ph.wq) if vcm else None))
+        del ph
+    h2d = sum(t.numel() * t.element_size() for t in (host[0].pos, host[0].flux, host[0].nq, host[0].rho,
+                                                      host[0].wq) if t is not None)
     d2h = 5 * 8 + 3 * 4            # counters, r_max, cell edge, flags
     torch.cuda.synchronize()
     pairs = 0
@@ -381,7 +417,7 @@ def run_e2e(est, batches, W, K):
     pairs += ppm.ppm_stats_host(est.ctx, est.it).pairs
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    return {"pairs": pairs, "seconds": dt, "h2d": h2d, "d2h": d2h}
+    return {"pairs": pairs, "seconds": dt, "h2d": h2d, "d2h": d2h, "steps": K}
 
 
 def run_batched(args, rank, world, local, dist):

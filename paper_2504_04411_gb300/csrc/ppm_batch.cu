@@ -254,7 +254,7 @@ struct BatchArgs {
 };
 
 template <int NCH, int NTC, bool NORMALS, bool VCM, int MAPPING>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<MAPPING>)
+__global__ void __launch_bounds__(kThreads, kMinBlocks<MAPPING, NTC>)
 k_batch_gather(GatherArgs a, BatchArgs bt)
 {
     __shared__ BlockShared<NCH, NTC, MAPPING> bsh;

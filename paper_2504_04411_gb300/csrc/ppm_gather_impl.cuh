@@ -15,9 +15,12 @@ namespace {
 constexpr int kThreads = 64;
 constexpr int kWarps = kThreads / 32;
 // resident blocks per SM that the traversals are register-budgeted for
-// (64 / 80 / 128 / 102 registers a thread), scaled with the block size
-template <int MAPPING>
-constexpr int kMinBlocks = (MAPPING == 0 ? 8 : (MAPPING == 1 ? 6 : (MAPPING == 2 ? 4 : 5))) * (128 / kThreads);
+// (64 / 80 / 128 / 102 registers a thread), scaled with the block size;
+// halved for three tested channels, whose 3x larger shared accumulators
+// cap the resident blocks anyway (and whose sums need the registers)
+template <int MAPPING, int NTC = 1>
+constexpr int kMinBlocks =
+    (MAPPING == 0 ? 8 : (MAPPING == 1 ? 6 : (MAPPING == 2 ? 4 : 5))) * (128 / kThreads) / (NTC == 3 ? 2 : 1);
 constexpr int kNormalDotMin = 8064;   // 127^2 / 2: cosine > ~0.5
 
 // arrays shared by all hit points of a launch (state is [slot][nh])
@@ -825,7 +828,7 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
 
 // one context: one block per kThreads hit points
 template <int NCH, int NTC, bool NORMALS, bool VCM, int MAPPING, bool FEAT = false>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<MAPPING>)
+__global__ void __launch_bounds__(kThreads, kMinBlocks<MAPPING, NTC>)
 k_gather_update(GatherArgs a, Prob pr)
 {
     __shared__ BlockShared<NCH, NTC, MAPPING> bsh;
