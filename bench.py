@@ -430,11 +430,12 @@ def run_batched(args, rank, world, local, dist):
     its = [[s.photons(i, "cuda") for s in scenes] for i in range(1, W + K + 1)]
     torch.cuda.synchronize()
     if args.mapping is not None and args.cell_factor is not None:
-        tuned = {"mapping": args.mapping, "cell_factors": [args.cell_factor] * len(scenes)}
+        tuned = {"mapping": args.mapping, "cell_factors": [args.cell_factor] * len(scenes), "tile": 64}
     else:
         tuned = autotune.tune_batch(scenes, hps, its[:3])
     params = ppm.ppm_default_params()
     params.mapping = tuned["mapping"]
+    params.tile = tuned["tile"]
     b = ppm.Batch(hps, [s.r0 for s in scenes], [s.J for s in scenes], params=params,
                   cell_factors=tuned["cell_factors"])
     for i in range(W):
@@ -500,7 +501,8 @@ def run_batched(args, rank, world, local, dist):
                                    "Gaussian lobes and step-edge shadows, ~150 photons per disk",
                        "hit_points": sum(s.nh for s in scenes), "photons_per_iter": sum(s.J for s in scenes),
                        "l2": "inputs larger than L2", "parallelism": "single GPU, one persistent launch",
-                       "mapping": tuned["mapping"], "cuda_graph": True},
+                       "mapping": tuned["mapping"], "cell_factor": tuned["cell_factors"][0],
+                       "tile_hit_points": tuned["tile"], "cuda_graph": True},
             "iterations_per_sec": K / total_s, "gather_ms": gather_ms, "gpu_launches": launches * K,
             "roofline": roof, "roofline_other": other, "clocks": clk,
             "vs_plain": {"value": plain_pairs / plain_s, "unit": UNIT,

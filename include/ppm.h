@@ -106,7 +106,10 @@ typedef struct {
                            3 = union walk with one pair queue per warp and
                            fixed-point group sums (one tested channel; with
                            rgb_test it runs as 0) */
-    int32_t reserved[6];
+    int32_t tile;       /* batches: hit points per tile of the persistent
+                           gather, a multiple of 64 in [64, 1024]; 0 = 64.
+                           Contexts ignore it.  Results do not depend on it. */
+    int32_t reserved[5];
 } ppm_params;
 
 /* Per-iteration counters of the last ppm_gather_test_update. */
@@ -276,8 +279,9 @@ int ppm_mlp_pack(const float* master, void* blob, void* stream);
  * factor a problem's results are bit-identical to a context's.  One
  * iteration of all of them is one grid build over all photons (the
  * problem id is mixed into the bucket hash and checked in the gather) and
- * ONE persistent gather launch whose resident blocks pull 64-hit-point
- * tiles from an atomic queue, heaviest problems first.  From the second
+ * ONE persistent gather launch whose resident blocks pull tiles of
+ * params->tile hit points (64 by default) from an atomic queue, heaviest
+ * problems first.  From the second
  * iteration on, the whole iteration is replayed as a CUDA graph on a
  * private stream ordered after the caller's stream. */
 typedef struct ppm_batch ppm_batch;

@@ -10,7 +10,8 @@ class is measured once per machine.
   then the gather of the next ones, CUDA events on the current stream);
 * ``tune_batch`` times every candidate on the whole batch (one persistent
   launch hides the small problems' latency behind the large ones, so
-  per-problem timings would mislead).
+  per-problem timings would mislead), then the tile sizes of the persistent
+  gather for the best one.
 """
 from __future__ import annotations
 
@@ -23,6 +24,7 @@ import torch
 from . import ppm
 
 CANDIDATES = ((0, 0.5), (0, 0.6), (0, 0.75), (0, 1.0), (1, 0.5), (1, 1.0))
+TILES = (64, 128, 256)       # batch tile sizes (hit points), tried for the best traversal
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 
@@ -87,8 +89,22 @@ def tune(hp, batches, r0: float, key: str | None = None, cache: str | None = DEF
     return dict(ent, key=key)
 
 
+def _time_batch(scenes, hps, photon_lists, mapping, cf, tile) -> float:
+    p = ppm.ppm_default_params()
+    p.mapping, p.tile = mapping, tile
+    b = ppm.Batch(hps, [s.r0 for s in scenes], [s.J for s in scenes], params=p,
+                  cell_factors=[cf] * len(scenes))
+    b.step(photon_lists[0])
+    ms = []
+    for it in photon_lists[1:]:
+        b.step(it)
+        ms.append(b.stats()[0].gather_ms)
+    b.close()
+    return sum(ms) / len(ms)
+
+
 def tune_batch(scenes, hps, photon_lists, cache: str | None = DEFAULT_CACHE,
-               candidates=CANDIDATES) -> dict:
+               candidates=CANDIDATES, tiles=TILES) -> dict:
     """Traversal and cell factor of a batch, timed on the batch itself.
 
     In one persistent launch the small problems' latencies hide behind the
@@ -97,30 +113,24 @@ def tune_batch(scenes, hps, photon_lists, cache: str | None = DEFAULT_CACHE,
     measured by the events the batch records around its gather launch).
     scenes: objects with nh, J, r0; hps: their hit points; photon_lists:
     >= 2 iterations, each a list with one photon batch per problem.
-    Returns {"mapping": m, "cell_factors": [...], "ms": {...}, "key": ...}."""
+    Returns {"mapping": m, "cell_factors": [...], "tile": t, "ms": {...},
+    "key": ...}."""
     key = "batch-" + "-".join(size_class(s.nh, s.J, s.r0) for s in scenes[:4]) + f"-n{len(scenes)}"
     data = _load(cache) if cache else {}
     ent = data.get(key)
     if ent is None:
-        times = {}
-        for m, cf in candidates:
-            p = ppm.ppm_default_params()
-            p.mapping = m
-            b = ppm.Batch(hps, [s.r0 for s in scenes], [s.J for s in scenes], params=p,
-                          cell_factors=[cf] * len(scenes))
-            b.step(photon_lists[0])
-            ms = []
-            for it in photon_lists[1:]:
-                b.step(it)
-                ms.append(b.stats()[0].gather_ms)
-            b.close()
-            times[f"{m},{cf}"] = sum(ms) / len(ms)
+        times = {f"{m},{cf},{tiles[0]}": _time_batch(scenes, hps, photon_lists, m, cf, tiles[0])
+                 for m, cf in candidates}
         best = min(times, key=times.get)
-        m, cf = best.split(",")
-        ent = {"mapping": int(m), "cell_factor": float(cf), "ms": times}
+        m, cf, _ = best.split(",")
+        for t in tiles[1:]:
+            times[f"{m},{cf},{t}"] = _time_batch(scenes, hps, photon_lists, int(m), float(cf), t)
+        best = min(times, key=times.get)
+        m, cf, t = best.split(",")
+        ent = {"mapping": int(m), "cell_factor": float(cf), "tile": int(t), "ms": times}
         if cache:
             data = _load(cache)
             data[key] = ent
             _store(cache, data)
     return {"mapping": ent["mapping"], "cell_factors": [ent["cell_factor"]] * len(scenes),
-            "ms": ent["ms"], "key": key}
+            "tile": ent.get("tile", 64), "ms": ent["ms"], "key": key}

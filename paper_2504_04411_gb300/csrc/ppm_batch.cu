@@ -4,7 +4,8 @@
 //   one pack pass over all photons (the problem id is mixed into the bucket
 //   hash and carried in every record), one stable radix sort, one cell-range
 //   pass, one permute, and ONE persistent gather launch: resident blocks pull
-//   tiles of kThreads hit points of one problem from an atomic queue, heaviest
+//   tiles of one problem (params.tile hit points, run as blocks of kThreads in
+//   turn; the autotuner picks the size) from an atomic queue, heaviest
 //   problems first, and run the same gather / F-test / update as a single
 //   context (bit-identical results for the same mapping and cell factor).
 // From the second iteration on the whole sequence is replayed as a CUDA
@@ -280,7 +281,9 @@ k_batch_gather(GatherArgs a, BatchArgs bt)
         pr.pid = (uint32_t)p;
         pr.inv_r0 = 0.f;
         pr.log_iter = 0.f;
-        gather_block<NCH, NTC, NORMALS, VCM, MAPPING, true>(a, pr, T.y, T.z, bsh);
+        // a tile is one or more blocks' worth of hit points, done in turn
+        for (int64_t h0 = T.y; h0 < T.z; h0 += kThreads)
+            gather_block<NCH, NTC, NORMALS, VCM, MAPPING, true>(a, pr, h0, T.z, bsh);
     }
 }
 
@@ -487,6 +490,8 @@ int ppm_batch_create(int32_t n_problems, const ppm_hitpoints* hp, const float* r
     if (prm.channels != 1 && prm.channels != 3) return PPM_EINVAL;
     if (prm.rgb_test && prm.channels != 3) return PPM_EINVAL;
     if (prm.mapping < 0 || prm.mapping > 3 || prm.n_vm < 0.f) return PPM_EINVAL;
+    if (prm.tile < 0 || prm.tile > 1024 || prm.tile % kThreads != 0) return PPM_EINVAL;
+    const int64_t tile_hits = prm.tile > 0 ? prm.tile : kThreads;
     const int P = n_problems;
     bool any_nq = false, all_nq = true;
     for (int p = 0; p < P; ++p) {
@@ -593,7 +598,7 @@ int ppm_batch_create(int32_t n_problems, const ppm_hitpoints* hp, const float* r
             rc = ppm_fcrit_fill(tab, 1, kFcCap, (double)J[p], prm.alpha_f, st);
         }
         if (rc) break;
-        // tiles of kThreads hit points, problems with the most photons per disk
+        // tiles of tile_hits hit points, problems with the most photons per disk
         // (J r0^2) first so the long tiles start early
         std::vector<int> order(P);
         for (int p = 0; p < P; ++p) order[p] = p;
@@ -602,9 +607,9 @@ int ppm_batch_create(int32_t n_problems, const ppm_hitpoints* hp, const float* r
         });
         std::vector<int4> tiles;
         for (int p : order)
-            for (int64_t h = 0; h < b->hp_n[p]; h += kThreads) {
+            for (int64_t h = 0; h < b->hp_n[p]; h += tile_hits) {
                 const int64_t h0 = b->hp_off[p] + h;
-                const int64_t he = b->hp_off[p] + std::min<int64_t>(b->hp_n[p], h + kThreads);
+                const int64_t he = b->hp_off[p] + std::min<int64_t>(b->hp_n[p], h + tile_hits);
                 tiles.push_back(make_int4(p, (int)h0, (int)he, 0));
             }
         b->ntiles = (int)tiles.size();

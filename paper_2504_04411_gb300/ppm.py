@@ -38,7 +38,7 @@ class ppm_params(ctypes.Structure):
                 ("rmin_ratio", ctypes.c_float), ("cell_factor", ctypes.c_float),
                 ("channels", ctypes.c_int32), ("rgb_test", ctypes.c_int32),
                 ("vcm", ctypes.c_int32), ("n_vm", ctypes.c_float),
-                ("mapping", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("mapping", ctypes.c_int32), ("tile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class ppm_iter_stats(ctypes.Structure):

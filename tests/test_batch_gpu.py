@@ -85,6 +85,31 @@ def test_batch_bit_identical_to_single_contexts(mapping):
         est.close()
 
 
+@pytest.mark.parametrize("tile", [128, 192, 1024])
+def test_batch_tile_size_does_not_change_results(tile):
+    """Larger tiles (several 64-hit-point blocks in turn, ragged ends) give
+    the same state and estimate as the default tiles, bit for bit."""
+    scenes = _problems()
+    iters = 3
+    _, _, s64, st64, L64, _ = _run_batch(scenes, iters, _params(mapping=0))
+    _, _, sT, stT, LT, _ = _run_batch(scenes, iters, _params(mapping=0, tile=tile))
+    for p in range(len(scenes)):
+        for i in range(iters):
+            for k in s64[i][p]:
+                assert np.array_equal(s64[i][p][k], sT[i][p][k]), (tile, p, i, k)
+            assert stT[i][p].pairs == st64[i][p].pairs
+        assert np.array_equal(L64[p], LT[p])
+
+
+def test_batch_rejects_bad_tile_sizes():
+    from paper_2504_04411_gb300 import ppm
+    scenes = _problems()[:2]
+    hps = [s.hitpoints("cuda") for s in scenes]
+    for tile in (-64, 32, 100, 2048):
+        with pytest.raises(ppm.PPMError):
+            ppm.Batch(hps, [s.r0 for s in scenes], [s.J for s in scenes], params=_params(tile=tile))
+
+
 def test_batch_rejects_bad_iterations():
     from paper_2504_04411_gb300 import ppm
     scenes = _problems()[:2]
