@@ -105,7 +105,9 @@ typedef struct {
                            cells (32 / 64-entry in-disk queues per lane),
                            3 = union walk with one pair queue per warp and
                            fixed-point group sums (one tested channel; with
-                           rgb_test it runs as 0) */
+                           rgb_test it runs as 0), 4 = a warp per hit point
+                           with shuffle-reduced group sums (one flux channel;
+                           with channels = 3 it runs as 0) */
     int32_t tile;       /* batches: hit points per tile of the persistent
                            gather, a multiple of 64 in [64, 1024]; 0 = 64.
                            Contexts ignore it.  Results do not depend on it. */
@@ -276,7 +278,9 @@ int ppm_mlp_pack(const float* master, void* blob, void* stream);
  * A batch holds n_problems independent problem instances (hit points,
  * radii, per-iteration photons, window statistics, estimates), each
  * exactly as one context would hold it: for the same mapping and cell
- * factor a problem's results are bit-identical to a context's.  One
+ * factor a problem's results are bit-identical to a context's (traversal
+ * 4: identical counts, windows, radii and decisions; its lanes' partial
+ * sums, and so the rounding of the window sums, can differ).  One
  * iteration of all of them is one grid build over all photons (the
  * problem id is mixed into the bucket hash and checked in the gather) and
  * ONE persistent gather launch whose resident blocks pull tiles of

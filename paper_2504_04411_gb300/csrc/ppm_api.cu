@@ -310,7 +310,7 @@ int ppm_create(const ppm_hitpoints* hp, float r0, float alpha, const ppm_params*
     if (prm.rgb_test && prm.channels != 3) return PPM_EINVAL;
     if (prm.vcm && hp->n > 0 && (!hp->rho || !hp->nq)) return PPM_EINVAL;
     if (prm.n_vm < 0.f) return PPM_EINVAL;
-    if (prm.mapping < 0 || prm.mapping > 3) return PPM_EINVAL;
+    if (prm.mapping < 0 || prm.mapping > 4) return PPM_EINVAL;
 
     ppm_ctx* c = new (std::nothrow) ppm_ctx();
     if (!c) return PPM_ENOMEM;

@@ -338,6 +338,21 @@ __global__ void k_batch_radiance(int64_t n, int64_t off, int nch, const double* 
 }
 
 // ---- the iteration ---------------------------------------------------------
+// traversal 4 exists for one flux channel only
+template <int NCH, int NTC, bool NORMALS, bool VCM>
+void launch_batch_warp_per_hit(ppm_batch* b, const GatherArgs& a, const BatchArgs& bt)
+{
+    if constexpr (NCH == 1) k_batch_gather<1, NTC, NORMALS, VCM, 4><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
+}
+
+template <int NCH, int NTC, bool NORMALS, bool VCM>
+cudaError_t batch_warp_per_hit_occupancy(int* per_sm)
+{
+    if constexpr (NCH == 1)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch_gather<1, NTC, NORMALS, VCM, 4>, kThreads, 0);
+    return cudaErrorInvalidValue;
+}
+
 template <int NCH, int NTC, bool NORMALS, bool VCM>
 int launch_batch_gather(ppm_batch* b, const GatherArgs& a, const BatchArgs& bt)
 {
@@ -345,6 +360,7 @@ int launch_batch_gather(ppm_batch* b, const GatherArgs& a, const BatchArgs& bt)
     if (m == 1) k_batch_gather<NCH, NTC, NORMALS, VCM, 1><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
     else if (m == 2) k_batch_gather<NCH, NTC, NORMALS, VCM, 2><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
     else if (m == 3 && NTC == 1) k_batch_gather<NCH, 1, NORMALS, VCM, 3><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
+    else if (m == 4 && NCH == 1) launch_batch_warp_per_hit<NCH, NTC, NORMALS, VCM>(b, a, bt);
     else k_batch_gather<NCH, NTC, NORMALS, VCM, 0><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
     PPM_LAUNCH_CHECK();
     return PPM_OK;
@@ -359,6 +375,7 @@ int gather_occupancy(ppm_batch* b)
     if (m == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gather<NCH, NTC, NORMALS, VCM, 1>, kThreads, 0);
     else if (m == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gather<NCH, NTC, NORMALS, VCM, 2>, kThreads, 0);
     else if (m == 3 && NTC == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gather<NCH, 1, NORMALS, VCM, 3>, kThreads, 0);
+    else if (m == 4 && NCH == 1) e = batch_warp_per_hit_occupancy<NCH, NTC, NORMALS, VCM>(&per_sm);
     else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gather<NCH, NTC, NORMALS, VCM, 0>, kThreads, 0);
     if (e != cudaSuccess) { cudaGetLastError(); return 1; }
     return per_sm > 0 ? per_sm : 1;
@@ -489,7 +506,7 @@ int ppm_batch_create(int32_t n_problems, const ppm_hitpoints* hp, const float* r
     if (!(prm.rmin_ratio >= 0.f && prm.rmin_ratio < 1.f)) return PPM_EINVAL;
     if (prm.channels != 1 && prm.channels != 3) return PPM_EINVAL;
     if (prm.rgb_test && prm.channels != 3) return PPM_EINVAL;
-    if (prm.mapping < 0 || prm.mapping > 3 || prm.n_vm < 0.f) return PPM_EINVAL;
+    if (prm.mapping < 0 || prm.mapping > 4 || prm.n_vm < 0.f) return PPM_EINVAL;
     if (prm.tile < 0 || prm.tile > 1024 || prm.tile % kThreads != 0) return PPM_EINVAL;
     const int64_t tile_hits = prm.tile > 0 ? prm.tile : kThreads;
     const int P = n_problems;

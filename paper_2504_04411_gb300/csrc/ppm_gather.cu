@@ -37,7 +37,11 @@
 //      pairs go to one queue per warp (ballot + prefix) and are classified
 //      32 at a time by any lane, accumulating into the owner's group sums
 //      as 64-bit fixed point with shared-memory atomics (exact and
-//      order-independent, hence deterministic); one tested channel.
+//      order-independent, hence deterministic); one tested channel;
+//   4  warp per hit point: the warp takes its 32 hit points in turn, the
+//      lanes split each trimmed row segment's photons into per-lane partial
+//      sums, and a shuffle reduce-scatter gathers the 36 group sums into
+//      the hit point's slots; one flux channel (otherwise it runs as 0).
 // A context that writes the proposer's features always runs traversal 0,
 // compiled separately so the other kernels carry none of that code.
 #include "ppm_gather_impl.cuh"
@@ -55,6 +59,12 @@ __global__ void k_radiance(int64_t nh, int nch, const double* __restrict__ tau,
 }
 
 template <int NCH, int NTC, bool NORMALS, bool VCM>
+void launch_warp_per_hit(ppm_ctx* c, const GatherArgs& a, const Prob& pr, unsigned nb)
+{
+    if constexpr (NCH == 1) k_gather_update<1, NTC, NORMALS, VCM, 4><<<nb, kThreads, 0, c->stream>>>(a, pr);
+}
+
+template <int NCH, int NTC, bool NORMALS, bool VCM>
 int launch_gather(ppm_ctx* c, const GatherArgs& a, const Prob& pr)
 {
     const unsigned nb = (unsigned)((c->nh + kThreads - 1) / kThreads);
@@ -67,6 +77,8 @@ int launch_gather(ppm_ctx* c, const GatherArgs& a, const Prob& pr)
         k_gather_update<NCH, NTC, NORMALS, VCM, 2><<<nb, kThreads, 0, c->stream>>>(a, pr);
     else if (m == 3 && NTC == 1)   // traversal 3 tests one channel
         k_gather_update<NCH, 1, NORMALS, VCM, 3><<<nb, kThreads, 0, c->stream>>>(a, pr);
+    else if (m == 4 && NCH == 1)   // traversal 4 gathers one flux channel
+        launch_warp_per_hit<NCH, NTC, NORMALS, VCM>(c, a, pr, nb);
     else
         k_gather_update<NCH, NTC, NORMALS, VCM, 0><<<nb, kThreads, 0, c->stream>>>(a, pr);
     PPM_LAUNCH_CHECK();

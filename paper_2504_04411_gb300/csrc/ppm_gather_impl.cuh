@@ -15,12 +15,13 @@ namespace {
 constexpr int kThreads = 64;
 constexpr int kWarps = kThreads / 32;
 // resident blocks per SM that the traversals are register-budgeted for
-// (64 / 80 / 128 / 102 registers a thread), scaled with the block size;
+// (64 / 80 / 128 / 102 / 85 registers a thread), scaled with the block size;
 // halved for three tested channels, whose 3x larger shared accumulators
 // cap the resident blocks anyway (and whose sums need the registers)
 template <int MAPPING, int NTC = 1>
 constexpr int kMinBlocks =
-    (MAPPING == 0 ? 8 : (MAPPING == 1 ? 6 : (MAPPING == 2 ? 4 : 5))) * (128 / kThreads) / (NTC == 3 ? 2 : 1);
+    (MAPPING == 0 ? 8 : (MAPPING == 1 || MAPPING == 4 ? 6 : (MAPPING == 2 ? 4 : 5))) * (128 / kThreads) /
+    (NTC == 3 ? 2 : 1);
 constexpr int kNormalDotMin = 8064;   // 127^2 / 2: cosine > ~0.5
 
 // arrays shared by all hit points of a launch (state is [slot][nh])
@@ -341,6 +342,7 @@ struct BlockShared {
     typename std::conditional<MAPPING == 1 || MAPPING == 2, UnionSmem<MAPPING == 2 ? 64 : 32>, Empty>::type us;
     typename std::conditional<MAPPING == 3, PairSmem, Empty>::type ps;
     typename std::conditional<MAPPING == 3, FixSmem<NCH>, Empty>::type fx;
+    typename std::conditional<MAPPING == 4, Smem<NTC>, Empty>::type lp;   // lanes' partial sums
 };
 
 // this iteration's sums of one hit point, read where they are kept
@@ -490,6 +492,108 @@ __device__ __noinline__ void write_features(const GatherArgs& a, const Prob& pr,
 // The hit points [h0, h_end) (at most one block's worth, h0 + tid for this
 // thread) of problem pr: gather, test, update; block-wide reductions into
 // pr's counters.  Ends with a block barrier, so it can be called in a loop.
+// Reduce-scatter of N values (N a power of two, <= 32) over the warp by
+// recursive halving: at each step a lane keeps half of its values, adds its
+// partner's copy of that half and passes on the other half.  Returns, on
+// lane l, the warp sum of value l / (32 / N).  N - 1 shuffles for N values
+// (plus log2(32 / N) for the lanes that end up sharing a value).
+template <int N, typename T>
+__device__ __forceinline__ T warp_reduce_scatter(T (&v)[N], int lane)
+{
+    static_assert(N >= 1 && N <= 32 && (N & (N - 1)) == 0, "N: a power of two up to 32");
+#pragma unroll
+    for (int half = N / 2, off = 16; half >= 1; half >>= 1, off >>= 1) {
+        const bool upper = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const T send = upper ? v[i] : v[i + half];
+            const T keep = upper ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+    T t = v[0];
+#pragma unroll
+    for (int off = 16 / N; off >= 1; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    return t;
+}
+
+__device__ __forceinline__ float4 shfl_f4(float4 v, int src)
+{
+    v.x = __shfl_sync(0xffffffffu, v.x, src);
+    v.y = __shfl_sync(0xffffffffu, v.y, src);
+    v.z = __shfl_sync(0xffffffffu, v.z, src);
+    v.w = __shfl_sync(0xffffffffu, v.w, src);
+    return v;
+}
+
+// Traversal 4: hit point Hj (lane j's, owner thread `owner`) by the whole
+// warp.  The warp walks its trimmed rows; the lanes split each segment's
+// photons and accumulate into their own column of lp; then the 36 group
+// sums are reduced across the warp with shuffles into the owner's slots of
+// sm.  One flux channel.
+template <int NTC, bool NORMALS, bool VCM, bool BATCH>
+__device__ __forceinline__ void gather_warp_hit(const GatherArgs& a, const Hit& Hj, const GridGeom& G, CellBox b,
+                                                Smem<NTC>& lp, Smem<NTC>& sm, int tid, int lane, int owner,
+                                                Acc<1>& acc)
+{
+    static_assert(NTC == 1, "traversal 4 tests one channel");
+    const int B = 1 << G.lb;
+    if (b.ix1 - b.ix0 >= B || b.iy1 - b.iy0 >= B || b.iz1 - b.iz0 >= B) {
+        if (lane == 0) atomicOr(a.err, 1);
+        b.ix1 = min(b.ix1, b.ix0 + B - 1); b.iy1 = min(b.iy1, b.iy0 + B - 1); b.iz1 = min(b.iz1, b.iz0 + B - 1);
+    }
+    const RowCull rcu = row_cull(Hj, G, b);
+    for (int iz = b.iz0; iz <= b.iz1; ++iz) {
+        const float gz = slab_gap(Hj.P.z, iz, G, rcu.eps);
+        const float rz2 = rcu.rc2 - gz * gz;
+        if (rz2 + rcu.slack < 0.f) continue;
+        for (int iy = b.iy0; iy <= b.iy1; ++iy) {
+            const float gy = slab_gap(Hj.P.y, iy, G, rcu.eps);
+            const float ryz2 = rz2 - gy * gy;
+            if (ryz2 + rcu.slack < 0.f) continue;
+            const float half = sqrtf(fmaxf(ryz2, 0.f) + rcu.slack) + rcu.eps;
+            const int xa = max(b.ix0, ppm_cell_coord(__fsub_rn(Hj.P.x, half), G.inv_h));
+            const int xb = min(b.ix1, ppm_cell_coord(__fadd_rn(Hj.P.x, half), G.inv_h));
+            int ix = xa;
+            while (ix <= xb) {
+                const int ixe = min(xb, ix | (B - 1));
+                const uint32_t b0 = ppm_bucket(ix, iy, iz, G);
+                const uint32_t s = __ldg(a.cell_start + b0);
+                const uint32_t e = __ldg(a.cell_start + b0 + (uint32_t)(ixe - ix) + 1u);
+                if (lane == 0) acc.cand += e - s;
+                for (uint32_t p = s + (uint32_t)lane; p < e; p += 32u) {
+                    const float4 X = __ldg(a.rec0 + p);
+                    float dx, dy, dz;
+                    if (in_disk(Hj, X, dx, dy, dz))
+                        gather_pair<1, NTC, NORMALS, VCM, BATCH>(a, Hj, lp, tid, acc, p, X, dx, dy, dz);
+                }
+                ix = ixe + 1;
+            }
+        }
+    }
+    // this lane's column -> registers (cleared for the next hit point)
+    float v[32];
+    uint32_t c[16];
+#pragma unroll
+    for (int g = 0; g < PPM_NG; ++g) {
+        const float2 q = lp.SQ[0][g][tid];
+        v[g] = q.x;
+        v[PPM_NG + g] = q.y;
+        c[g] = lp.c[g][tid];
+        lp.SQ[0][g][tid] = make_float2(0.f, 0.f);
+        lp.c[g][tid] = 0u;
+    }
+#pragma unroll
+    for (int i = 2 * PPM_NG; i < 32; ++i) v[i] = 0.f;
+#pragma unroll
+    for (int i = PPM_NG; i < 16; ++i) c[i] = 0u;
+    const float t = warp_reduce_scatter<32>(v, lane);        // lane l: value l
+    const uint32_t ct = warp_reduce_scatter<16>(c, lane);    // lane l: count l / 2
+    if (lane < PPM_NG) sm.SQ[0][lane][owner].x = t;
+    else if (lane < 2 * PPM_NG) sm.SQ[0][lane - PPM_NG][owner].y = t;
+    if ((lane & 1) == 0 && (lane >> 1) < PPM_NG) sm.c[lane >> 1][owner] = ct;
+}
+
 // FEAT: also write the proposer's features (a separate instantiation: the
 // call alone costs the feature-free kernel about 10% through register
 // allocation in the cell walk)
@@ -498,6 +602,7 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
                                              int64_t h_end, BlockShared<NCH, NTC, MAPPING>& bsh)
 {
     static_assert(MAPPING != 3 || NTC == 1, "traversal 3 tests one channel");
+    static_assert(MAPPING != 4 || NCH == 1, "traversal 4 gathers one flux channel");
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int64_t h = h0 + tid;
     const bool live = h < h_end;
@@ -509,6 +614,13 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
             sm.c[g][tid] = 0u;
 #pragma unroll
             for (int c = 0; c < NTC; ++c) sm.SQ[c][g][tid] = make_float2(0.f, 0.f);
+        }
+        if constexpr (MAPPING == 4) {
+#pragma unroll
+            for (int g = 0; g < PPM_NG; ++g) {
+                bsh.lp.c[g][tid] = 0u;
+                bsh.lp.SQ[0][g][tid] = make_float2(0.f, 0.f);
+            }
         }
     } else {
 #pragma unroll
@@ -553,6 +665,27 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
     const FixScale fs = fix_scale(MAPPING == 3 ? G.psimax : 1.f);
     if constexpr (MAPPING == 0) {
         if (live) gather_own<NCH, NTC, NORMALS, VCM, BATCH>(a, H, G, b, sm, tid, acc);
+    } else if constexpr (MAPPING == 4) {
+        __syncwarp();
+        for (int j = 0; j < 32; ++j) {
+            if (!__shfl_sync(0xffffffffu, (int)live, j)) continue;   // warp-uniform
+            Hit Hj;
+            Hj.P = shfl_f4(H.P, j);
+            Hj.U = shfl_f4(H.U, j);
+            Hj.V = shfl_f4(H.V, j);
+            Hj.r = __shfl_sync(0xffffffffu, H.r, j);
+            Hj.r2 = __shfl_sync(0xffffffffu, H.r2, j);
+            Hj.inv_eta = __shfl_sync(0xffffffffu, H.inv_eta, j);
+            Hj.nqh = __shfl_sync(0xffffffffu, H.nqh, j);
+            Hj.pid = H.pid;
+            CellBox bj;
+            bj.ix0 = __shfl_sync(0xffffffffu, b.ix0, j); bj.ix1 = __shfl_sync(0xffffffffu, b.ix1, j);
+            bj.iy0 = __shfl_sync(0xffffffffu, b.iy0, j); bj.iy1 = __shfl_sync(0xffffffffu, b.iy1, j);
+            bj.iz0 = __shfl_sync(0xffffffffu, b.iz0, j); bj.iz1 = __shfl_sync(0xffffffffu, b.iz1, j);
+            bj.rc = __shfl_sync(0xffffffffu, b.rc, j);
+            gather_warp_hit<NTC, NORMALS, VCM, BATCH>(a, Hj, G, bj, bsh.lp, sm, tid, lane, w * 32 + j, acc);
+        }
+        __syncwarp();
     } else if constexpr (MAPPING == 3) {
         PairSmem& ps = bsh.ps;
         auto& fx = bsh.fx;

@@ -51,7 +51,7 @@ def _run_batch(scenes, iters, params, cfs=None):
     return hps, phs, states, stats, L, graph
 
 
-@pytest.mark.parametrize("mapping", [0, 1, 3])
+@pytest.mark.parametrize("mapping", [0, 1, 3, 4])
 def test_batch_matches_oracle_per_problem(mapping):
     scenes = _problems()
     iters = 4
@@ -65,23 +65,37 @@ def test_batch_matches_oracle_per_problem(mapping):
         assert rep.diverged <= 2
 
 
-@pytest.mark.parametrize("mapping", [0, 1, 3])
+@pytest.mark.parametrize("mapping", [0, 1, 3, 4])
 def test_batch_bit_identical_to_single_contexts(mapping):
-    import torch
+    """Traversals 0-3 visit a hit point's photons in the same order in a
+    batch as in a context, so the state is bit-identical.  Traversal 4 splits
+    a cell's photons over the lanes by position, and a batch's cells can
+    also hold other problems' photons (skipped): the lanes' partial sums, and
+    so the rounding of the window sums, can differ.  Counts, windows, radii
+    and decisions stay identical."""
     from paper_2504_04411_gb300 import ppm
     scenes = _problems()
     iters = 4
     cfs = [0.5, 1.0, 2.0, 1.0, 0.5, 1.0]
     hps, phs, states, stats, L, _ = _run_batch(scenes, iters, _params(mapping=mapping), cfs)
+    exact = ("r", "t", "counts")
     for p, sc in enumerate(scenes):
         est = ppm.Estimator(hps[p], sc.r0, params=_params(mapping=mapping, cell_factor=cfs[p]))
         for i in range(iters):
             est.step(phs[i][p])
             one = {k: v.cpu().numpy() for k, v in est.state().items()}
             for k in one:
-                assert np.array_equal(one[k], states[i][p][k]), (p, i, k)
+                if mapping != 4 or k in exact:
+                    assert np.array_equal(one[k], states[i][p][k]), (p, i, k)
+                else:
+                    assert np.allclose(one[k], states[i][p][k], rtol=1e-5, atol=1e-6 * np.abs(one[k]).max()), \
+                        (p, i, k)
             assert est.stats().pairs == stats[i][p].pairs
-        assert np.array_equal(est.radiance().cpu().numpy(), L[p])
+        Lc = est.radiance().cpu().numpy()
+        if mapping != 4:
+            assert np.array_equal(Lc, L[p])
+        else:
+            assert np.allclose(Lc, L[p], rtol=1e-5, atol=1e-6 * np.abs(Lc).max())
         est.close()
 
 

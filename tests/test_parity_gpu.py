@@ -57,7 +57,7 @@ def test_fcrit_other_alpha_and_monotone():
 
 
 # --------------------------------------------------------- plane scenes ----
-MAPPINGS = [0, 1, 2, 3]
+MAPPINGS = [0, 1, 2, 3, 4]
 
 
 @pytest.mark.parametrize("mapping", MAPPINGS)
