@@ -23,7 +23,7 @@ import torch
 
 from . import ppm
 
-CANDIDATES = ((0, 0.5), (0, 0.6), (0, 0.75), (0, 1.0), (1, 0.5), (1, 1.0))
+CANDIDATES = ((0, 0.5), (0, 0.6), (0, 0.75), (0, 1.0), (1, 0.5), (1, 1.0), (4, 0.5), (4, 1.0))
 TILES = (64, 128, 256)       # batch tile sizes (hit points), tried for the best traversal
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
