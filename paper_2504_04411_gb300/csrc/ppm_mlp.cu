@@ -14,7 +14,7 @@
 // shrinks the radius of a hit point the test did not just reject when the
 // network calls it doomed: r <- max(r max(exp(o0), min_ratio), bound); the
 // window is cleared as on a rejection.  The F-test still runs every
-// iteration on whatever radius a hit point has: it stays the judge.
+// iteration on whatever radius a hit point has: it keeps the final say.
 //
 // Inference (k_mlp_forward, k_mlp_propose) runs on the tensor cores: a warp
 // takes 16 samples through all three layers with mma.sync m16n8k16 BF16
