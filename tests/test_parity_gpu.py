@@ -174,6 +174,46 @@ def test_translated_box_scene(offset, mapping):
     assert rep.diverged <= 3
 
 
+# hit point minus photon offsets with exact FP32 values around a disk of
+# radius 1/4, and the group each one must land in (annulus * 6 + sector;
+# inner iff 2 rho^2 < r^2, sector k = [60k, 60(k+1)) degrees of atan2(yv, yu),
+# ties as the classification rule fixes them)
+_TIES = [((0.25, 0.0), 6), ((-0.25, 0.0), 9), ((0.0, 0.25), 7), ((0.0, -0.25), 10),   # d^2 == r^2: inside
+         ((0.125, 0.125), 6), ((-0.125, 0.125), 8), ((-0.125, -0.125), 9),            # 2 rho^2 == r^2: outer
+         ((0.125, -0.125), 11),
+         ((0.125, 0.0), 0), ((-0.125, 0.0), 3), ((0.0, 0.125), 1), ((0.0, -0.125), 4),  # yv == 0 / yu == 0
+         ((0.0, 0.0), 1),                                                             # the centre
+         ((0.25 + 2.0 ** -20, 0.0), None), ((0.0, -0.25 - 2.0 ** -20), None)]          # just outside
+
+
+@pytest.mark.parametrize("mapping", MAPPINGS)
+def test_exact_boundary_photons(mapping):
+    """Photons exactly on the disk edge, the annulus boundary and the sector
+    edges: every traversal puts each in the group the rule fixes (closed
+    disk, boundary to the outer annulus), as the oracle does."""
+    import torch
+    from paper_2504_04411_gb300 import ppm
+    centres = [(0.5, 0.5), (0.125, 0.875)]          # disks 0.53 apart: no shared photons
+    hp = synth.HitPoints(torch.tensor([[x, y, 0.0] for x, y in centres], dtype=torch.float32).cuda(),
+                         torch.tensor([[1.0, 0.0, 0.0]] * 2).cuda(), torch.tensor([[0.0, 1.0, 0.0]] * 2).cuda(),
+                         None, None)
+    pos = [[x - dx, y - dy, 0.0] for x, y in centres for (dx, dy), _ in _TIES]
+    J = len(pos)
+    ph = synth.Photons(torch.tensor(pos, dtype=torch.float32).cuda(),
+                       torch.full((J,), 1.0 / J, dtype=torch.float32).cuda(), None, None, None)
+    want = np.zeros(12, np.int64)
+    for _, g in _TIES:
+        if g is not None:
+            want[g] += 1
+    params = _params(mapping=mapping, alpha_f=1e-12)     # no rejection: the window keeps the counts
+    states, stats, L = run_gpu(hp, [ph], 0.25, params=params)
+    ref = O.run(hp.numpy(), synth.stack_numpy([ph]), 0.25, 1, alpha_f=1e-12)
+    assert np.array_equal(ref.counts[0], np.stack([want, want]))
+    assert np.array_equal(states[0]["counts"], np.stack([want, want]).astype(np.int32))
+    assert stats[0]["pairs"] == 2 * int(want.sum())
+    compare(states, stats, L, ref, 1)
+
+
 # ------------------------------------------------------------ edge cases ---
 def test_empty_iterations_and_single_hit_point():
     import torch
