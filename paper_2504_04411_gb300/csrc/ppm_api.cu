@@ -208,7 +208,7 @@ void free_ctx(ppm_ctx* c)
     cudaFree(c->cnt); cudaFree(c->S); cudaFree(c->Q);
     cudaFree(c->cell_start);
     cudaFree(c->rec0); cudaFree(c->rec1); cudaFree(c->aux);
-    cudaFree(c->pack0); cudaFree(c->pack1); cudaFree(c->pack_aux);
+    cudaFree(c->pack);
     ppm_sort_scratch_free(&c->sort);
     cudaFree(c->geom_dev); cudaFree(c->rmax); cudaFree(c->fc);
     cudaFree(c->counters); cudaFree(c->err_dev); cudaFree(c->feat);

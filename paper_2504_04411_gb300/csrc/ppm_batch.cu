@@ -85,8 +85,8 @@ struct ppm_batch {
     SortScratch sort;
     int tbits = 0, lb = 3;
     uint32_t* cell_start = nullptr;
-    float4 *pack0 = nullptr, *pack1 = nullptr, *rec0 = nullptr, *rec1 = nullptr;
-    uint4 *pack_aux = nullptr, *aux = nullptr;
+    float4 *pack = nullptr, *rec0 = nullptr, *rec1 = nullptr;   // pack: a photon's records side by side
+    uint4* aux = nullptr;
     int32_t* err = nullptr;
     // graph
     cudaGraph_t graph = nullptr;
@@ -149,8 +149,8 @@ void free_batch(ppm_batch* b)
     if (b->ptab_h) cudaFreeHost(b->ptab_h);
     if (b->sc_h) cudaFreeHost(b->sc_h);
     ppm_sort_scratch_free(&b->sort);
-    cudaFree(b->cell_start); cudaFree(b->pack0); cudaFree(b->pack1); cudaFree(b->rec0);
-    cudaFree(b->rec1); cudaFree(b->pack_aux); cudaFree(b->aux); cudaFree(b->err);
+    cudaFree(b->cell_start); cudaFree(b->pack); cudaFree(b->rec0);
+    cudaFree(b->rec1); cudaFree(b->aux); cudaFree(b->err);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     if (b->ev_staged) cudaEventDestroy(b->ev_staged);
@@ -195,9 +195,11 @@ template <int NCH, bool VCM, bool PSIMAX>
 __global__ void __launch_bounds__(256)
 k_batch_pack(const int4* __restrict__ blocks, const PhotonPtrs* __restrict__ ptab,
              GridGeom* __restrict__ geom, uint32_t* __restrict__ keys,
-             uint32_t* __restrict__ vals, float4* __restrict__ pack0, float4* __restrict__ pack1,
-             uint4* __restrict__ pack_aux)
+             uint32_t* __restrict__ vals, float4* __restrict__ pack)
 {
+    // a photon's records side by side: x y z psi | (R G B rho_vm) | aux
+    constexpr bool REC1 = NCH == 3 || VCM;
+    constexpr int S = 2 + (REC1 ? 1 : 0);
     const int4 B = blocks[blockIdx.x];          // (problem, first local index, count, offset)
     const int i = B.y + threadIdx.x;
     const int p = B.x;
@@ -216,10 +218,12 @@ k_batch_pack(const int4* __restrict__ blocks, const PhotonPtrs* __restrict__ pta
         R = pt.flux[i];
         psi = R;
     }
-    pack0[o] = make_float4(x, y, z, psi);
-    if (NCH == 3 || VCM) pack1[o] = make_float4(R, G, Bc, VCM ? pt.rho[2ll * i] : 0.f);
-    pack_aux[o] = make_uint4(pt.nq ? pt.nq[i] : 0u, VCM ? pt.wq[i] : 0u,
-                             VCM ? __float_as_uint(pt.rho[2ll * i + 1]) : 0u, (uint32_t)p);
+    float4* rec = pack + o * S;
+    rec[0] = make_float4(x, y, z, psi);
+    if constexpr (REC1) rec[1] = make_float4(R, G, Bc, VCM ? pt.rho[2ll * i] : 0.f);
+    reinterpret_cast<uint4*>(rec)[S - 1] = make_uint4(pt.nq ? pt.nq[i] : 0u, VCM ? pt.wq[i] : 0u,
+                                                      VCM ? __float_as_uint(pt.rho[2ll * i + 1]) : 0u,
+                                                      (uint32_t)p);
     keys[o] = ppm_bucket(ppm_cell_coord(x, g.inv_h), ppm_cell_coord(y, g.inv_h),
                          ppm_cell_coord(z, g.inv_h), g);
     vals[o] = (uint32_t)o;
@@ -446,7 +450,7 @@ int enqueue_iteration(ppm_batch* b)
         const bool pm = b->prm.mapping == 3;
         auto pack = [&](auto kern) {
             kern<<<b->npack, 256, 0, st>>>(b->pack_blocks, b->ptab_d, b->geom, b->sort.keys, b->sort.vals,
-                                           b->pack0, b->pack1, b->pack_aux);
+                                           b->pack);
         };
         if (b->nch == 3) {
             if (vcm) pm ? pack(k_batch_pack<3, true, true>) : pack(k_batch_pack<3, true, false>);
@@ -468,8 +472,7 @@ int enqueue_iteration(ppm_batch* b)
     ++launches;
     if (n > 0) {
         const bool rec1 = b->nch == 3 || b->prm.vcm;
-        rc = ppm_permute_launch(n, b->sort.vals, b->pack0, rec1 ? b->pack1 : nullptr, b->pack_aux,
-                                b->rec0, rec1 ? b->rec1 : nullptr, b->aux, st);
+        rc = ppm_permute_launch(n, b->sort.vals, b->pack, b->rec0, rec1 ? b->rec1 : nullptr, b->aux, st);
         if (rc) return rc;
         ++launches;
     }
@@ -561,9 +564,9 @@ int ppm_batch_create(int32_t n_problems, const ppm_hitpoints* hp, const float* r
               dal(&b->rmin_dev, P) && dal(&b->Jf, P) && dal(&b->nvm, P) && dal(&b->bound, P) &&
               dal(&b->fc, (int64_t)P * (kFcCap + 1)) && dal(&b->counters, 4ll * P) &&
               dal(&b->pairs_total, P) && dal(&b->head, 1) && dal(&b->ptab_d, P) && dal(&b->sc_d, 1) &&
-              dal(&b->err, 1) && dal(&b->pack0, np) && dal(&b->rec0, np) && dal(&b->pack_aux, np) &&
-              dal(&b->aux, np);
-    if (ok && (b->nch == 3 || prm.vcm)) ok = dal(&b->pack1, np) && dal(&b->rec1, np);
+              dal(&b->err, 1) && dal(&b->rec0, np) && dal(&b->aux, np) &&
+              dal(&b->pack, np * ((b->nch == 3 || prm.vcm) ? 3 : 2));
+    if (ok && (b->nch == 3 || prm.vcm)) ok = dal(&b->rec1, np);
     if (ok) ok = cudaMallocHost(&b->ptab_h, P * sizeof(PhotonPtrs)) == cudaSuccess &&
                  cudaMallocHost(&b->sc_h, sizeof(IterScalars)) == cudaSuccess;
     if (ok) ok = ppm_sort_scratch_reserve(&b->sort, np > 0 ? np : 1) == PPM_OK;

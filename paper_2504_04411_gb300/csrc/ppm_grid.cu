@@ -56,9 +56,12 @@ __global__ void __launch_bounds__(256)
 k_pack_keys(int64_t n, const float* __restrict__ pos, const float* __restrict__ flux,
             const uint32_t* __restrict__ nq, const float* __restrict__ rho,
             const uint32_t* __restrict__ wq, GridGeom* __restrict__ geom,
-            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
-            float4* __restrict__ pack0, float4* __restrict__ pack1, uint4* __restrict__ pack_aux)
+            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, float4* __restrict__ pack)
 {
+    // a photon's records side by side (x y z psi | R G B rho_vm | aux), so
+    // that the permute's random read of one photon fetches whole sectors
+    constexpr bool REC1 = NCH == 3 || VCM;
+    constexpr int S = 1 + (REC1 ? 1 : 0) + (AUX ? 1 : 0);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const GridGeom g = *geom;
     float vmax = 0.f;
@@ -74,12 +77,12 @@ k_pack_keys(int64_t n, const float* __restrict__ pos, const float* __restrict__ 
         psi = R;
         vmax = psi;
     }
-    pack0[i] = make_float4(x, y, z, psi);
-    if (NCH == 3 || VCM)
-        pack1[i] = make_float4(R, G, B, VCM ? rho[2 * i] : 0.f);
-    if (AUX)
-        pack_aux[i] = make_uint4(nq ? nq[i] : 0u, VCM ? wq[i] : 0u,
-                                 VCM ? __float_as_uint(rho[2 * i + 1]) : 0u, 0u);
+    float4* rec = pack + i * S;
+    rec[0] = make_float4(x, y, z, psi);
+    if constexpr (REC1) rec[1] = make_float4(R, G, B, VCM ? rho[2 * i] : 0.f);
+    if constexpr (AUX)
+        reinterpret_cast<uint4*>(rec)[S - 1] = make_uint4(nq ? nq[i] : 0u, VCM ? wq[i] : 0u,
+                                                          VCM ? __float_as_uint(rho[2 * i + 1]) : 0u, 0u);
     const int ix = ppm_cell_coord(x, g.inv_h);
     const int iy = ppm_cell_coord(y, g.inv_h);
     const int iz = ppm_cell_coord(z, g.inv_h);
@@ -120,19 +123,20 @@ k_cell_start(const uint32_t* __restrict__ keys, int64_t n, uint32_t T,
     }
 }
 
+// records of packed photon vals[i] (stride 1 + REC1 + AUX float4s) into
+// the gather's separate sorted arrays
 template <bool REC1, bool AUX>
 __global__ void __launch_bounds__(256)
-k_permute(int64_t n, const uint32_t* __restrict__ vals,
-          const float4* __restrict__ pack0, const float4* __restrict__ pack1,
-          const uint4* __restrict__ pack_aux, float4* __restrict__ rec0,
-          float4* __restrict__ rec1, uint4* __restrict__ aux)
+k_permute(int64_t n, const uint32_t* __restrict__ vals, const float4* __restrict__ pack,
+          float4* __restrict__ rec0, float4* __restrict__ rec1, uint4* __restrict__ aux)
 {
+    constexpr int S = 1 + (REC1 ? 1 : 0) + (AUX ? 1 : 0);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint32_t j = vals[i];
-    rec0[i] = pack0[j];
-    if (REC1) rec1[i] = pack1[j];
-    if (AUX) aux[i] = pack_aux[j];
+    const float4* src = pack + (int64_t)vals[i] * S;
+    rec0[i] = __ldg(src);
+    if constexpr (REC1) rec1[i] = __ldg(src + 1);
+    if constexpr (AUX) aux[i] = __ldg(reinterpret_cast<const uint4*>(src) + (S - 1));
 }
 
 template <int NCH, bool AUX, bool VCM>
@@ -141,11 +145,11 @@ void launch_pack(ppm_ctx* c, const ppm_photons* ph, unsigned nb)
     if (c->prm.mapping == 3)
         k_pack_keys<NCH, AUX, VCM, true><<<nb, 256, 0, c->stream>>>(
             ph->n, ph->pos, ph->flux, ph->nq, ph->rho, ph->wq, c->geom_dev,
-            c->sort.keys, c->sort.vals, c->pack0, c->pack1, c->pack_aux);
+            c->sort.keys, c->sort.vals, c->pack);
     else
         k_pack_keys<NCH, AUX, VCM, false><<<nb, 256, 0, c->stream>>>(
             ph->n, ph->pos, ph->flux, ph->nq, ph->rho, ph->wq, c->geom_dev,
-            c->sort.keys, c->sort.vals, c->pack0, c->pack1, c->pack_aux);
+            c->sort.keys, c->sort.vals, c->pack);
 }
 
 int reserve_photons(ppm_ctx* c, int64_t n)
@@ -153,18 +157,18 @@ int reserve_photons(ppm_ctx* c, int64_t n)
     int rc = ppm_sort_scratch_reserve(&c->sort, n > 0 ? n : 1);
     if (rc) return rc;
     if (n <= c->ph_cap) return PPM_OK;
-    cudaFree(c->pack0); cudaFree(c->pack1); cudaFree(c->pack_aux);
+    cudaFree(c->pack);
     cudaFree(c->rec0); cudaFree(c->rec1); cudaFree(c->aux);
-    c->pack0 = c->pack1 = c->rec0 = c->rec1 = nullptr;
-    c->pack_aux = c->aux = nullptr;
+    c->pack = c->rec0 = c->rec1 = nullptr;
+    c->aux = nullptr;
     c->ph_cap = 0;
     const int64_t cap = n + n / 4 + 1024;
     const bool rec1 = c->nch == 3 || c->prm.vcm;
-    if (cudaMalloc(&c->pack0, cap * sizeof(float4)) != cudaSuccess ||
+    // packed records: up to 3 float4 a photon (the aux record depends on
+    // whether the iteration brings normals)
+    if (cudaMalloc(&c->pack, cap * (rec1 ? 3 : 2) * sizeof(float4)) != cudaSuccess ||
         cudaMalloc(&c->rec0, cap * sizeof(float4)) != cudaSuccess ||
-        (rec1 && (cudaMalloc(&c->pack1, cap * sizeof(float4)) != cudaSuccess ||
-                  cudaMalloc(&c->rec1, cap * sizeof(float4)) != cudaSuccess)) ||
-        cudaMalloc(&c->pack_aux, cap * sizeof(uint4)) != cudaSuccess ||
+        (rec1 && cudaMalloc(&c->rec1, cap * sizeof(float4)) != cudaSuccess) ||
         cudaMalloc(&c->aux, cap * sizeof(uint4)) != cudaSuccess) {
         cudaGetLastError();
         return PPM_ENOMEM;
@@ -232,8 +236,7 @@ int ppm_grid_build(ppm_ctx* c, const ppm_photons* ph)
     if (rc) return rc;
     if (n > 0) {
         const bool rec1 = c->nch == 3 || vcm;
-        rc = ppm_permute_launch(n, c->sort.vals, c->pack0, rec1 ? c->pack1 : nullptr,
-                                aux ? c->pack_aux : nullptr, c->rec0, rec1 ? c->rec1 : nullptr,
+        rc = ppm_permute_launch(n, c->sort.vals, c->pack, c->rec0, rec1 ? c->rec1 : nullptr,
                                 aux ? c->aux : nullptr, c->stream);
         if (rc) return rc;
     }
@@ -250,20 +253,19 @@ int ppm_cell_start_launch(const uint32_t* keys, int64_t n, uint32_t T, uint32_t*
     return PPM_OK;
 }
 
-int ppm_permute_launch(int64_t n, const uint32_t* vals, const float4* pack0, const float4* pack1,
-                       const uint4* pack_aux, float4* rec0, float4* rec1, uint4* aux,
-                       cudaStream_t st)
+int ppm_permute_launch(int64_t n, const uint32_t* vals, const float4* pack, float4* rec0, float4* rec1,
+                       uint4* aux, cudaStream_t st)
 {
     if (n <= 0) return PPM_OK;
     const unsigned nb = (unsigned)((n + 255) / 256);
     if (rec1 && aux)
-        k_permute<true, true><<<nb, 256, 0, st>>>(n, vals, pack0, pack1, pack_aux, rec0, rec1, aux);
+        k_permute<true, true><<<nb, 256, 0, st>>>(n, vals, pack, rec0, rec1, aux);
     else if (rec1)
-        k_permute<true, false><<<nb, 256, 0, st>>>(n, vals, pack0, pack1, pack_aux, rec0, rec1, aux);
+        k_permute<true, false><<<nb, 256, 0, st>>>(n, vals, pack, rec0, rec1, aux);
     else if (aux)
-        k_permute<false, true><<<nb, 256, 0, st>>>(n, vals, pack0, pack1, pack_aux, rec0, rec1, aux);
+        k_permute<false, true><<<nb, 256, 0, st>>>(n, vals, pack, rec0, rec1, aux);
     else
-        k_permute<false, false><<<nb, 256, 0, st>>>(n, vals, pack0, pack1, pack_aux, rec0, rec1, aux);
+        k_permute<false, false><<<nb, 256, 0, st>>>(n, vals, pack, rec0, rec1, aux);
     PPM_LAUNCH_CHECK();
     return PPM_OK;
 }

@@ -151,9 +151,7 @@ struct ppm_ctx {
     float4* rec0 = nullptr;
     float4* rec1 = nullptr;
     uint4* aux = nullptr;
-    float4* pack0 = nullptr;      // unsorted packed records
-    float4* pack1 = nullptr;
-    uint4* pack_aux = nullptr;
+    float4* pack = nullptr;       // unsorted records, a photon's side by side
     SortScratch sort;
     GridGeom* geom_dev = nullptr;     // written on the device by the build
     int lb = 2;
@@ -207,9 +205,8 @@ int ppm_table_bits(int64_t n, int lb);
 int ppm_cell_start_launch(const uint32_t* keys, int64_t n, uint32_t T, uint32_t* cell_start,
                           cudaStream_t st);
 // packed records gathered into sorted order (rec1 / aux when non-NULL)
-int ppm_permute_launch(int64_t n, const uint32_t* vals, const float4* pack0, const float4* pack1,
-                       const uint4* pack_aux, float4* rec0, float4* rec1, uint4* aux,
-                       cudaStream_t st);
+int ppm_permute_launch(int64_t n, const uint32_t* vals, const float4* pack, float4* rec0, float4* rec1,
+                       uint4* aux, cudaStream_t st);
 // ppm_api.cu: hit points -> Hilbert-sorted internal layout (synchronizes st)
 int ppm_prepare_hitpoints(const ppm_hitpoints* hp, bool with_rho, uint32_t* orig, float4* pos,
                           float4* u, float4* v, cudaStream_t st);
