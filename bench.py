@@ -583,15 +583,16 @@ def run_reference(args):
     threads = os.cpu_count() or 1
     os.environ.setdefault("OMP_NUM_THREADS", str(threads))
     W, K = args.warmup, args.steps
+    kw = {"vcm": True, "k": 0.9} if args.config == "vcm" else {}
     ph_np = synth.stack_numpy([sc.photons(1, "cpu")])
-    _, dt = oracle_sample(sc, ph_np, hp_np, 64, seed=0)
+    _, dt = oracle_sample(sc, ph_np, hp_np, 64, seed=0, **kw)
     per_step_s = min(2.0, 150.0 / (W + K))
     n = int(min(hp_np["pos"].shape[0], max(16, 64 * per_step_s / max(dt, 1e-3))))
     pairs = 0
     secs = 0.0
     for i in range(W + K):
         ph_np = synth.stack_numpy([sc.photons(i + 1, "cpu")])
-        p, dt = oracle_sample(sc, ph_np, hp_np, n, seed=100 + i)
+        p, dt = oracle_sample(sc, ph_np, hp_np, n, seed=100 + i, **kw)
         if i >= W:
             pairs += p
             secs += dt
