@@ -120,7 +120,9 @@ typedef struct {
     int32_t flags;         /* device error flags; bit 0: a sphere spanned more
                               cells than a hash block (results incomplete);
                               bit 1: a window length outside the F_c table
-                              (from ppm_set_state), clamped */
+                              (from ppm_set_state), clamped; bit 2: a wait
+                              between the blocks of the grid's sort gave up
+                              (never expected; results unspecified) */
     int64_t pairs;         /* in-disk photon/hit-point pairs gathered */
     int64_t candidates;    /* photons visited in the scanned cells */
     int64_t rejects;       /* hit points whose null hypothesis was rejected */
@@ -220,10 +222,14 @@ int ppm_f_critical(int64_t J, double alpha_f, int32_t t_max, double* out, void* 
  * ppm_build_grid: pairs with equal keys keep their input order.  keys_in,
  * vals_in: n uint32 each (device, read only); keys_out, vals_out: n uint32
  * each (device, written; may alias the inputs).  n in [0, 2^32 - 1).
- * Scratch (2n + 256 ceil(n/2048) words) comes from cudaMallocAsync on the
- * stream and is released with cudaFreeAsync, so the call does not block.
- * PPM_EINVAL for bad sizes or NULL pointers with n > 0, PPM_ENOMEM if the
- * scratch cannot be allocated. */
+ * One kernel per 8-bit pass: the blocks of a pass wait for the counts of
+ * earlier blocks (decoupled look-back).  Every such wait ends, because a
+ * block waits only for blocks that started before it; each is capped all
+ * the same, and were a cap ever reached the output order would be
+ * unspecified.  Scratch (2n words + 2 KB per 2048 pairs + 4 KB) comes from
+ * cudaMallocAsync on the stream and is released with cudaFreeAsync, so the
+ * call does not block.  PPM_EINVAL for bad sizes or NULL pointers with
+ * n > 0, PPM_ENOMEM if the scratch cannot be allocated. */
 int ppm_sort_pairs(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
                    uint32_t* vals_out, int64_t n, int32_t bits, void* stream);
 
@@ -327,7 +333,8 @@ const char* ppm_strerror(int code);
 
 /* ---- no-allocation variant (the paper has no counterpart) ----------------
  * ppm_sort_pairs_noalloc: the same stable radix sort as ppm_sort_pairs, with
- * the same arguments, results and error codes, for callers that must not
+ * the same arguments, results and error codes (computed by three kernels a
+ * pass, with no waits between blocks), for callers that must not
  * allocate device memory while they run -- work recorded into a CUDA graph
  * (stream capture forbids cudaMalloc), real-time loops that cannot pay for
  * an allocator call or its implicit synchronization, hosts whose device

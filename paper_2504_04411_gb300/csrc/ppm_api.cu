@@ -649,26 +649,32 @@ int ppm_sort_pairs(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* k
     if (vals_out != vals_in)
         PPM_CUDA(cudaMemcpyAsync(vals_out, vals_in, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
     if (n == 1) return PPM_OK;
+    // scratch: alternate keys and values, the look-back words, the digit
+    // counts and an error word (the single-pass form of the grid's sort)
     const int64_t ntiles = (n + 2047) / 2048;
-    const int64_t hist = 256 * ntiles;
-    const int64_t part = hist / 4096 + 2;
-    uint32_t* scratch = nullptr;
-    const size_t words = (size_t)(2 * n + hist + part);
-    if (cudaMallocAsync((void**)&scratch, words * sizeof(uint32_t), st) != cudaSuccess) {
+    const int64_t status_words = 32 + 256 * ntiles;
+    const size_t off_status = ((size_t)2 * n * sizeof(uint32_t) + 255) & ~(size_t)255;
+    const size_t off_digit = off_status + (size_t)status_words * sizeof(unsigned long long);
+    const size_t off_err = off_digit + 4 * 256 * sizeof(uint32_t);
+    const size_t bytes = off_err + 256;
+    unsigned char* scratch = nullptr;
+    if (cudaMallocAsync((void**)&scratch, bytes, st) != cudaSuccess) {
         cudaGetLastError();
         return PPM_ENOMEM;
     }
     SortScratch s;
     s.keys = keys_out;
     s.vals = vals_out;
-    s.keys_alt = scratch;
-    s.vals_alt = scratch + n;
-    s.hist = scratch + 2 * n;
-    s.partials = scratch + 2 * n + hist;
+    s.keys_alt = reinterpret_cast<uint32_t*>(scratch);
+    s.vals_alt = reinterpret_cast<uint32_t*>(scratch) + n;
+    s.status = reinterpret_cast<unsigned long long*>(scratch + off_status);
+    s.digit = reinterpret_cast<uint32_t*>(scratch + off_digit);
     s.cap = n;
-    s.hist_cap = hist;
-    s.part_cap = part;
-    int rc = ppm_radix_sort_pairs(&s, n, bits, st);
+    s.status_cap = status_words;
+    int32_t* err = reinterpret_cast<int32_t*>(scratch + off_err);
+    int rc = PPM_OK;
+    if (cudaMemsetAsync(err, 0, sizeof(int32_t), st) != cudaSuccess) { cudaGetLastError(); rc = PPM_ECUDA; }
+    if (rc == PPM_OK) rc = ppm_radix_sort_pairs_lookback(&s, n, bits, err, st);
     if (rc == PPM_OK && s.keys != keys_out) {   // odd number of passes
         if (cudaMemcpyAsync(keys_out, s.keys, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
             cudaMemcpyAsync(vals_out, s.vals, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess)

@@ -463,9 +463,9 @@ int enqueue_iteration(ppm_batch* b)
         ++launches;
         // the ping-pong pointer sequence of the sort is recorded into the
         // graph as it is at capture time, so every replay is consistent
-        int rc = ppm_radix_sort_pairs(&b->sort, n, b->tbits, st);
+        int rc = ppm_radix_sort_pairs_lookback(&b->sort, n, b->tbits, b->err, st);
         if (rc) return rc;
-        launches += 5 * ((b->tbits + 7) / 8);
+        launches += 2 + (b->tbits + 7) / 8;
     }
     int rc = ppm_cell_start_launch(b->sort.keys, n, T, b->cell_start, st);
     if (rc) return rc;

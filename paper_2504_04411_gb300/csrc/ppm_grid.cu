@@ -229,7 +229,7 @@ int ppm_grid_build(ppm_ctx* c, const ppm_photons* ph)
             else launch_pack<1, false, false>(c, ph, nb);
         }
         PPM_LAUNCH_CHECK();
-        rc = ppm_radix_sort_pairs(&c->sort, n, c->tbits, c->stream);
+        rc = ppm_radix_sort_pairs_lookback(&c->sort, n, c->tbits, c->err_dev, c->stream);
         if (rc) return rc;
     }
     rc = ppm_cell_start_launch(c->sort.keys, n, T, c->cell_start, c->stream);
@@ -241,7 +241,7 @@ int ppm_grid_build(ppm_ctx* c, const ppm_photons* ph)
         if (rc) return rc;
     }
     c->n_ph = n;
-    c->launches_build = 2 + (n > 0 ? 2 + 5 * ((c->tbits + 7) / 8) : 0);
+    c->launches_build = 2 + (n > 0 ? 2 + 2 + (c->tbits + 7) / 8 : 0);
     return PPM_OK;
 }
 

@@ -93,9 +93,12 @@ struct SortScratch {
     uint32_t* vals_alt = nullptr;
     uint32_t* hist = nullptr;       // 256 * ntiles
     uint32_t* partials = nullptr;   // scan block partials
+    unsigned long long* status = nullptr;   // look-back words (single-pass form)
+    uint32_t* digit = nullptr;      // 4 x 256 digit counts / offsets (single-pass form)
     int64_t cap = 0;                // elements of each key/value array
     int64_t hist_cap = 0;
     int64_t part_cap = 0;
+    int64_t status_cap = 0;
 };
 
 // Stable LSD radix sort of (s->keys, s->vals)[0, n) on the low `bits` bits
@@ -103,6 +106,11 @@ struct SortScratch {
 // pointers are swapped with the alternates after each 8-bit pass).
 // Requires ppm_sort_scratch_reserve(s, >= n) first.
 int ppm_radix_sort_pairs(SortScratch* s, int64_t n, int bits, cudaStream_t st);
+// The same sort in one kernel per pass (decoupled look-back between the
+// blocks of a pass; the counts of every pass first).  A look-back wait that
+// gives up (it should never) sets bit 2 of *err (device).  Launches 2 +
+// ceil(bits / 8) kernels.
+int ppm_radix_sort_pairs_lookback(SortScratch* s, int64_t n, int bits, int32_t* err, cudaStream_t st);
 int ppm_sort_scratch_reserve(SortScratch* s, int64_t n);
 void ppm_sort_scratch_free(SortScratch* s);
 

@@ -2,7 +2,10 @@
 // and a device-wide exclusive scan, used to build the photon grid (cell key
 // + stable radix sort) and to sort hit points spatially.
 //
-// One pass per 8-bit digit, three kernels per pass:
+// Two forms of the same sort (same output: both are stable).
+//
+// Three kernels per 8-bit pass (ppm_radix_sort_pairs; no block waits for
+// another):
 //   hist    : per 2048-key tile, the digit histogram, stored digit-major
 //             (hist[d * ntiles + tile]) so that ...
 //   scan    : ... one flat exclusive scan gives every (digit, tile) its
@@ -10,6 +13,21 @@
 //   scatter : each warp ranks its 256 keys with __match_any_sync (peers with
 //             the same digit) in input order, warps are combined per digit in
 //             warp order, so equal digits keep their input order (stable).
+//
+// One kernel per pass after one counting pass for all of them
+// (ppm_radix_sort_pairs_lookback, used by the grid builds):
+//   counts  : every pass's global digit counts in one read of the keys, and
+//             their exclusive scans (one block);
+//   onesweep: each block takes the next tile number from a counter, ranks
+//             its tile as the scatter above does, and finds, per digit, how
+//             many keys of that digit earlier tiles hold by decoupled
+//             look-back: it publishes its own count at once (flag
+//             AGGREGATE), then walks back over earlier tiles' words adding
+//             counts until one carries an INCLUSIVE prefix, and publishes
+//             its own inclusive prefix.  A tile only waits for tiles with
+//             lower numbers, which took theirs earlier and are running, so
+//             every wait ends; each is still capped (kSpinLimit polls),
+//             after which bit 2 of *err is set and the order is unspecified.
 #include "ppm_internal.cuh"
 
 namespace {
@@ -89,6 +107,148 @@ k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ v
             const uint32_t pos = s_cnt[w][d[j]] + rank[j];
             kout[pos] = k[j];
             vout[pos] = v[j];
+        }
+    }
+}
+
+// ---- single-pass form ------------------------------------------------------
+constexpr unsigned long long kFlagAggregate = 1ull << 62;
+constexpr unsigned long long kFlagInclusive = 2ull << 62;
+constexpr unsigned long long kCountMask = (1ull << 62) - 1ull;
+constexpr int kSpinLimit = 1 << 22;
+constexpr int kStatusHead = 32;          // words before the per-tile words: [0] tile counter
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// every pass's digit counts (counts[p * 256 + d], zeroed by the caller)
+__global__ void __launch_bounds__(kSortThreads)
+k_digit_counts(const uint32_t* __restrict__ keys, int64_t n, int bits, uint32_t* __restrict__ counts)
+{
+    __shared__ uint32_t s_c[4][256];
+    const int npass = (bits + 7) / 8;
+    for (int i = threadIdx.x; i < 4 * 256; i += kSortThreads) (&s_c[0][0])[i] = 0u;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * kSortThreads + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kSortThreads) {
+        const uint32_t k = keys[i];
+        for (int p = 0; p < npass; ++p) {
+            const int nb = bits - 8 * p < 8 ? bits - 8 * p : 8;
+            atomicAdd(&s_c[p][(k >> (8 * p)) & ((1u << nb) - 1u)], 1u);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < npass * 256; i += kSortThreads) {
+        const uint32_t v = (&s_c[0][0])[i];
+        if (v) atomicAdd(counts + i, v);
+    }
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x);
+
+// counts[p][d] -> exclusive prefix over d, per pass (one block of 256)
+__global__ void __launch_bounds__(256)
+k_digit_offsets(uint32_t* __restrict__ counts, int npass)
+{
+    __shared__ uint32_t s_w[8];
+    const int d = threadIdx.x, lane = d & 31, w = d >> 5;
+    for (int p = 0; p < npass; ++p) {
+        const uint32_t x = counts[p * 256 + d];
+        const uint32_t inc = warp_incl_scan(x);
+        if (lane == 31) s_w[w] = inc;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int ww = 0; ww < w; ++ww) before += s_w[ww];
+        counts[p * 256 + d] = before + inc - x;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+k_radix_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                 uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
+                 uint32_t mask, const uint32_t* __restrict__ goff, unsigned long long* status,
+                 int32_t* err)
+{
+    __shared__ uint32_t s_cnt[kWarps][256];
+    __shared__ uint32_t s_base[256];
+    __shared__ int s_t;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    if (tid == 0) s_t = (int)atomicAdd(reinterpret_cast<unsigned*>(status), 1u);
+    for (int i = lane; i < 256; i += 32) s_cnt[w][i] = 0;
+    __syncthreads();
+    const int t = s_t;
+    // rank the tile's keys in input order (as k_radix_scatter)
+    const int64_t base = (int64_t)t * kTile + (int64_t)w * (32 * kSortItems);
+    uint32_t k[kSortItems], v[kSortItems], d[kSortItems], rank[kSortItems];
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const int64_t idx = base + j * 32 + lane;
+        const bool valid = idx < n;
+        k[j] = valid ? kin[idx] : 0u;
+        v[j] = valid ? vin[idx] : 0u;
+        d[j] = valid ? ((k[j] >> shift) & mask) : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d[j]);
+        const uint32_t before = __popc(peers & lt);
+        const uint32_t c = valid ? s_cnt[w][d[j]] : 0u;
+        rank[j] = c + before;
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) s_cnt[w][d[j]] = c + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {   // digit dg: the tile's count, per-warp prefixes, then earlier tiles by look-back
+        const int dg = tid;
+        uint32_t local = 0;
+#pragma unroll
+        for (int ww = 0; ww < kWarps; ++ww) {
+            const uint32_t c = s_cnt[ww][dg];
+            s_cnt[ww][dg] = local;
+            local += c;
+        }
+        unsigned long long* word = status + kStatusHead;
+        unsigned long long excl = 0;
+        if (t == 0) {
+            st_relaxed_u64(word + dg, kFlagInclusive | local);
+        } else {
+            st_relaxed_u64(word + (int64_t)t * 256 + dg, kFlagAggregate | local);
+            int q = t - 1, spins = 0;
+            while (q >= 0) {
+                const unsigned long long x = ld_relaxed_u64(word + (int64_t)q * 256 + dg);
+                const unsigned long long f = x & ~kCountMask;
+                if (f == 0ull) {
+                    if (++spins > kSpinLimit) { atomicOr(err, 4); break; }
+                    __nanosleep(32);
+                    continue;
+                }
+                excl += x & kCountMask;
+                if (f == kFlagInclusive) break;
+                --q;
+            }
+            st_relaxed_u64(word + (int64_t)t * 256 + dg, kFlagInclusive | (excl + local));
+        }
+        s_base[dg] = goff[dg] + (uint32_t)excl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        if (d[j] < 256u) {
+            // positions are in [0, n) unless a look-back wait gave up
+            const uint32_t pos = s_base[d[j]] + s_cnt[w][d[j]] + rank[j];
+            if ((int64_t)pos < n) {
+                kout[pos] = k[j];
+                vout[pos] = v[j];
+            }
         }
     }
 }
@@ -239,6 +399,16 @@ int ppm_sort_scratch_reserve(SortScratch* s, int64_t n)
         if (cudaMalloc(&s->hist, cap * sizeof(uint32_t)) != cudaSuccess) { cudaGetLastError(); return PPM_ENOMEM; }
         s->hist_cap = cap;
     }
+    const int64_t words = kStatusHead + 256 * (ntiles > 0 ? ntiles : 1);
+    if (words > s->status_cap) {
+        cudaFree(s->status); s->status = nullptr; s->status_cap = 0;
+        const int64_t cap = words + words / 4 + 256;
+        if (cudaMalloc(&s->status, cap * sizeof(unsigned long long)) != cudaSuccess) { cudaGetLastError(); return PPM_ENOMEM; }
+        s->status_cap = cap;
+    }
+    if (!s->digit) {
+        if (cudaMalloc(&s->digit, 4 * 256 * sizeof(uint32_t)) != cudaSuccess) { cudaGetLastError(); return PPM_ENOMEM; }
+    }
     if (part > s->part_cap) {
         cudaFree(s->partials); s->partials = nullptr; s->part_cap = 0;
         const int64_t cap = part + 64;
@@ -251,7 +421,7 @@ int ppm_sort_scratch_reserve(SortScratch* s, int64_t n)
 void ppm_sort_scratch_free(SortScratch* s)
 {
     cudaFree(s->keys); cudaFree(s->vals); cudaFree(s->keys_alt); cudaFree(s->vals_alt);
-    cudaFree(s->hist); cudaFree(s->partials);
+    cudaFree(s->hist); cudaFree(s->partials); cudaFree(s->status); cudaFree(s->digit);
     *s = SortScratch{};
 }
 
@@ -269,6 +439,34 @@ int ppm_radix_sort_pairs(SortScratch* s, int64_t n, int bits, cudaStream_t st)
         if (rc) return rc;
         k_radix_scatter<<<ntiles, kSortThreads, 0, st>>>(s->keys, s->vals, s->keys_alt, s->vals_alt,
                                                           n, shift, mask, s->hist, ntiles);
+        PPM_LAUNCH_CHECK();
+        uint32_t* t;
+        t = s->keys; s->keys = s->keys_alt; s->keys_alt = t;
+        t = s->vals; s->vals = s->vals_alt; s->vals_alt = t;
+    }
+    return PPM_OK;
+}
+
+int ppm_radix_sort_pairs_lookback(SortScratch* s, int64_t n, int bits, int32_t* err, cudaStream_t st)
+{
+    if (n <= 1 || bits <= 0) return PPM_OK;
+    if (n > 0xFFFFFFFFll || bits > 32 || n > s->cap || !s->status || !s->digit || !err) return PPM_EINVAL;
+    const int ntiles = (int)((n + kTile - 1) / kTile);
+    if (kStatusHead + 256ll * ntiles > s->status_cap) return PPM_EINVAL;
+    const int npass = (bits + 7) / 8;
+    PPM_CUDA(cudaMemsetAsync(s->digit, 0, (size_t)npass * 256 * sizeof(uint32_t), st));
+    const int cblocks = ntiles < 1024 ? ntiles : 1024;
+    k_digit_counts<<<cblocks, kSortThreads, 0, st>>>(s->keys, n, bits, s->digit);
+    PPM_LAUNCH_CHECK();
+    k_digit_offsets<<<1, 256, 0, st>>>(s->digit, npass);
+    PPM_LAUNCH_CHECK();
+    for (int p = 0; p < npass; ++p) {
+        const int shift = 8 * p;
+        const int nb = bits - shift < 8 ? bits - shift : 8;
+        const uint32_t mask = (1u << nb) - 1u;
+        PPM_CUDA(cudaMemsetAsync(s->status, 0, (size_t)(kStatusHead + 256ll * ntiles) * sizeof(unsigned long long), st));
+        k_radix_onesweep<<<ntiles, kSortThreads, 0, st>>>(s->keys, s->vals, s->keys_alt, s->vals_alt, n, shift,
+                                                         mask, s->digit + p * 256, s->status, err);
         PPM_LAUNCH_CHECK();
         uint32_t* t;
         t = s->keys; s->keys = s->keys_alt; s->keys_alt = t;
