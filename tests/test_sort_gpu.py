@@ -46,6 +46,19 @@ def test_sort_pairs_matches_stable_argsort(n, bits):
     assert np.array_equal(got_v, ref_v)
 
 
+def test_sort_pairs_many_tiles():
+    """20M pairs, 27-bit keys (4 passes, ~9,800 tiles waiting on their
+    predecessors' counts), few distinct high digits."""
+    rng = np.random.default_rng(11)
+    n, bits = 20_000_000, 27
+    keys = (rng.integers(0, 1 << 15, n, dtype=np.uint64) << np.uint64(12)).astype(np.uint32)
+    keys |= rng.integers(0, 1 << 12, n, dtype=np.uint32)
+    vals = np.arange(n, dtype=np.uint32)
+    got_k, got_v = _sort(keys, vals, bits)
+    ref_k, ref_v = _ref(keys, vals, bits)
+    assert np.array_equal(got_k, ref_k) and np.array_equal(got_v, ref_v)
+
+
 def test_sort_pairs_ignores_bits_above_width():
     rng = np.random.default_rng(5)
     keys = rng.integers(0, 1 << 32, 50_000, dtype=np.uint64).astype(np.uint32)
