@@ -117,6 +117,8 @@ constexpr unsigned long long kFlagInclusive = 2ull << 62;
 constexpr unsigned long long kCountMask = (1ull << 62) - 1ull;
 constexpr int kSpinLimit = 1 << 22;
 constexpr int kStatusHead = 32;          // words before the per-tile words: [0] tile counter
+constexpr int kSweepItems = 8;           // keys a thread in the single-pass kernel
+constexpr int kSweepTile = kSortThreads * kSweepItems;
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p)
 {
@@ -189,10 +191,10 @@ k_radix_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ 
     __syncthreads();
     const int t = s_t;
     // rank the tile's keys in input order (as k_radix_scatter)
-    const int64_t base = (int64_t)t * kTile + (int64_t)w * (32 * kSortItems);
-    uint32_t k[kSortItems], v[kSortItems], d[kSortItems], rank[kSortItems];
+    const int64_t base = (int64_t)t * kSweepTile + (int64_t)w * (32 * kSweepItems);
+    uint32_t k[kSweepItems], v[kSweepItems], d[kSweepItems], rank[kSweepItems];
 #pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
+    for (int j = 0; j < kSweepItems; ++j) {
         const int64_t idx = base + j * 32 + lane;
         const bool valid = idx < n;
         k[j] = valid ? kin[idx] : 0u;
@@ -241,7 +243,7 @@ k_radix_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ 
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
+    for (int j = 0; j < kSweepItems; ++j) {
         if (d[j] < 256u) {
             // positions are in [0, n) unless a look-back wait gave up
             const uint32_t pos = s_base[d[j]] + s_cnt[w][d[j]] + rank[j];
@@ -451,7 +453,7 @@ int ppm_radix_sort_pairs_lookback(SortScratch* s, int64_t n, int bits, int32_t* 
 {
     if (n <= 1 || bits <= 0) return PPM_OK;
     if (n > 0xFFFFFFFFll || bits > 32 || n > s->cap || !s->status || !s->digit || !err) return PPM_EINVAL;
-    const int ntiles = (int)((n + kTile - 1) / kTile);
+    const int ntiles = (int)((n + kSweepTile - 1) / kSweepTile);
     if (kStatusHead + 256ll * ntiles > s->status_cap) return PPM_EINVAL;
     const int npass = (bits + 7) / 8;
     PPM_CUDA(cudaMemsetAsync(s->digit, 0, (size_t)npass * 256 * sizeof(uint32_t), st));
