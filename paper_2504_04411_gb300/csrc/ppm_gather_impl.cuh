@@ -239,6 +239,25 @@ __device__ __forceinline__ float slab_gap(float p, int i, const GridGeom& G, flo
     return fmaxf(fmaxf(lo - p, p - hi) - eps, 0.f);
 }
 
+// this hit point's trimmed x-range of row (iy, iz) (the computation of
+// traversal 0's walk); empty (x0 > x1) for a row outside its cell box or
+// missing its sphere, and for a lane without a hit point
+__device__ __forceinline__ void row_xrange(const Hit& H, const GridGeom& G, const CellBox& b, const RowCull& rcu,
+                                           bool live, int iy, int iz, int& x0, int& x1)
+{
+    x0 = INT_MAX;
+    x1 = INT_MIN;
+    if (!live || iy < b.iy0 || iy > b.iy1 || iz < b.iz0 || iz > b.iz1) return;
+    const float gz = slab_gap(H.P.z, iz, G, rcu.eps);
+    const float rz2 = rcu.rc2 - gz * gz;
+    const float gy = slab_gap(H.P.y, iy, G, rcu.eps);
+    const float ryz2 = rz2 - gy * gy;
+    if (rz2 + rcu.slack < 0.f || ryz2 + rcu.slack < 0.f) return;
+    const float half = sqrtf(fmaxf(ryz2, 0.f) + rcu.slack) + rcu.eps;
+    x0 = max(b.ix0, ppm_cell_coord(__fsub_rn(H.P.x, half), G.inv_h));
+    x1 = min(b.ix1, ppm_cell_coord(__fadd_rn(H.P.x, half), G.inv_h));
+}
+
 // traversal 0: the thread walks its own cells
 template <int NCH, int NTC, bool NORMALS, bool VCM, bool BATCH>
 __device__ void gather_own(const GatherArgs& a, const Hit& H, const GridGeom& G, CellBox b,
@@ -687,6 +706,7 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
         }
         __syncwarp();
     } else if constexpr (MAPPING == 3) {
+        const RowCull rcu = row_cull(H, G, b);     // row trimming of the union walk
         PairSmem& ps = bsh.ps;
         auto& fx = bsh.fx;
         const unsigned full = 0xffffffffu;
@@ -733,10 +753,13 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
             int qn = 0;                     // warp-uniform queue length
             for (int iz = Z0; iz <= Z1; ++iz) {
                 for (int iy = Y0; iy <= Y1; ++iy) {
-                    const bool need = live && b.iy0 <= iy && iy <= b.iy1 && b.iz0 <= iz && iz <= b.iz1;
+                    // the union of the lanes' trimmed ranges of this row
+                    int tx0, tx1;
+                    row_xrange(H, G, b, rcu, live, iy, iz, tx0, tx1);
+                    const bool need = tx0 <= tx1;
                     if (!__any_sync(full, need)) continue;
-                    const int rx0 = __reduce_min_sync(full, need ? b.ix0 : INT_MAX);
-                    const int rx1 = __reduce_max_sync(full, need ? b.ix1 : INT_MIN);
+                    const int rx0 = __reduce_min_sync(full, need ? tx0 : INT_MAX);
+                    const int rx1 = __reduce_max_sync(full, need ? tx1 : INT_MIN);
                     int ix = rx0;
                     while (ix <= rx1) {
                         const int ixe = min(rx1, ix | (B - 1));
@@ -775,6 +798,7 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
             drain_pairs<NCH, NORMALS, VCM, BATCH>(a, ps, fx, fs, pr.pid, w, lane, qn);
         }
     } else {
+        const RowCull rcu = row_cull(H, G, b);     // row trimming of the union walk
         using US = UnionSmem<kQueue>;
         US& us = bsh.us;
         const unsigned full = 0xffffffffu;
@@ -790,10 +814,13 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
             int qlen = 0;
             for (int iz = Z0; iz <= Z1; ++iz) {
                 for (int iy = Y0; iy <= Y1; ++iy) {
-                    const bool need = live && b.iy0 <= iy && iy <= b.iy1 && b.iz0 <= iz && iz <= b.iz1;
+                    // the union of the lanes' trimmed ranges of this row
+                    int tx0, tx1;
+                    row_xrange(H, G, b, rcu, live, iy, iz, tx0, tx1);
+                    const bool need = tx0 <= tx1;
                     if (!__any_sync(full, need)) continue;
-                    const int rx0 = __reduce_min_sync(full, need ? b.ix0 : INT_MAX);
-                    const int rx1 = __reduce_max_sync(full, need ? b.ix1 : INT_MIN);
+                    const int rx0 = __reduce_min_sync(full, need ? tx0 : INT_MAX);
+                    const int rx1 = __reduce_max_sync(full, need ? tx1 : INT_MIN);
                     int ix = rx0;
                     while (ix <= rx1) {
                         const int ixe = min(rx1, ix | (B - 1));
