@@ -286,6 +286,33 @@ def test_argument_and_sequence_errors():
     est.close()
 
 
+def test_size_limits_are_refused():
+    """Sizes beyond the documented limits are refused with PPM_EINVAL before
+    any memory is touched (small real arrays stand behind the pointers)."""
+    import ctypes
+    import torch
+    from paper_2504_04411_gb300 import ppm
+    L = ppm.load()
+    buf = torch.zeros(64, device="cuda")
+    p = ctypes.c_void_p(buf.data_ptr())
+    out = ctypes.c_void_p()
+    hp = ppm.ppm_hitpoints(1 << 31, p, p, p, None, None)            # above 2^31 - 1 hit points
+    assert L.ppm_create(ctypes.byref(hp), 0.1, 0.75, None, None, ctypes.byref(out)) == ppm.PPM_EINVAL
+    assert not out.value
+    sc = synth.PlaneScene(nside=4, J=1000)
+    est = ppm.Estimator(sc.hitpoints("cuda"), 0.1)
+    ph = ppm.ppm_photons(0xfffffff1, 0xfffffff1, p, p, 1, 0, None, None, None)   # above 2^32 - 16 photons
+    assert L.ppm_build_grid(est.ctx, ctypes.byref(ph)) == ppm.PPM_EINVAL
+    ph = ppm.ppm_photons(-1, 1000, p, p, 1, 0, None, None, None)
+    assert L.ppm_build_grid(est.ctx, ctypes.byref(ph)) == ppm.PPM_EINVAL
+    assert L.ppm_iterate_host(est.ctx, ctypes.byref(ph), 1) == ppm.PPM_EINVAL
+    est.close()
+    assert L.ppm_sort_pairs(p, p, p, p, 0xffffffff, 8, None) == ppm.PPM_EINVAL   # n >= 2^32 - 1
+    assert L.ppm_sort_pairs_noalloc(p, p, p, p, ppm.PPM_NOALLOC_MAX_PAIRS + 1, 8, None) == ppm.PPM_EINVAL
+    assert L.ppm_f_critical(1, 0.01, 10, p, None) == ppm.PPM_EINVAL               # J < 2
+    assert L.ppm_mlp_forward(p, p, -1, p, None) == ppm.PPM_EINVAL
+
+
 def test_deterministic_and_resumable():
     """Two runs give bitwise-identical state; a context resumed from a
     checkpoint continues exactly like the straight run."""
