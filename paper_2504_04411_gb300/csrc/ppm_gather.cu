@@ -1,10 +1,11 @@
 // ppm_gather.cu -- per-hit-point gather, ANOVA F-test and update (Sec. 5.1
-// steps 2-4), hit points in spatial (Morton) order, 128 threads per block,
-// one thread per hit point.
+// steps 2-4), hit points in spatial (3D Hilbert) order, blocks of 64
+// threads, one hit point a thread in the epilogue.
 //
 // Per hit point h with radius r (this iteration's r_i):
-//   * the photons of the grid cells overlapping the sphere's bounding box
-//     are candidates; per candidate: closed-disk test d2 <= r^2 with
+//   * candidates: the photons of the grid cells overlapping the sphere's
+//     bounding box, each row of cells trimmed to the chord of the sphere at
+//     the row's nearest point; per candidate: closed-disk test d2 <= r^2 with
 //     dx = x_h - x_p, then the same-surface test (snorm8 normal dot > 8064),
 //     then the map of Eq. (map-function) y = (<x_h - x_p, u>, <x_h - x_p, v>),
 //     the equi-areal annulus (2 |y|^2 < r^2 -> inner) and the 60-degree

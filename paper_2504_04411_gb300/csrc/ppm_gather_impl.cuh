@@ -11,11 +11,10 @@
 
 namespace {
 
-
 constexpr int kThreads = 64;
 constexpr int kWarps = kThreads / 32;
-// resident blocks per SM that the traversals are register-budgeted for
-// (64 / 80 / 128 / 102 / 85 registers a thread), scaled with the block size;
+// resident blocks per SM that traversals 0-4 are register-budgeted for
+// (64 / 85 / 128 / 102 / 85 registers a thread), scaled with the block size;
 // halved for three tested channels, whose 3x larger shared accumulators
 // cap the resident blocks anyway (and whose sums need the registers)
 template <int MAPPING, int NTC = 1>
