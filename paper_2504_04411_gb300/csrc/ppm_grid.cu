@@ -1,13 +1,15 @@
-// ppm_grid.cu -- photon map of one iteration (Sec. 5.1: "build a range
-// search data structure of the light vertices"): a hashed uniform grid.
+// ppm_grid.cu -- photon map of one iteration (the range-search structure
+// over the light vertices that Sec. 5.1 builds first): a hashed uniform grid.
 //
 //   k_grid_geom  : cell edge h = cell_factor * max_h r_h, read from device
 //                  memory written by the previous update (no host sync);
 //   k_pack_keys  : one coalesced pass over the caller's photons: bucket key,
-//                  identity index, and the photon packed into 16-byte records;
+//                  identity index, and the photon's 16-byte records side by
+//                  side;
 //   radix sort   : stable, on the bucket bits (ppm_sort.cu);
-//   k_cell_start : cell_start[b] = first sorted photon with bucket >= b;
-//   k_permute    : packed records gathered into bucket order.
+//   k_cell_start : cell_start[b] = first sorted photon with bucket >= b
+//                  (each warp fills the empty-bucket gaps cooperatively);
+//   k_permute    : records gathered into bucket order, one array each.
 #include "ppm_internal.cuh"
 
 namespace {

@@ -1,6 +1,6 @@
 // ppm_noalloc.cu -- ppm_sort_pairs_noalloc: the stable radix sort of
-// ppm_sort_pairs with its scratch in a fixed device array instead of
-// memory allocated per call.
+// ppm_sort_pairs (in its three-kernel-per-pass form, same results) with its
+// scratch in a fixed device array instead of memory allocated per call.
 //
 // For callers that must not allocate device memory while they run: code
 // being recorded into a CUDA graph (stream capture forbids cudaMalloc),
