@@ -270,7 +270,10 @@ int ppm_mlp_forward(const void* blob, const float* X, int64_t n, float* Y, void*
 /* Gradient of scale * sum_s [0.5 M0 (o0 - Y0)^2 + M1 BCE(o1, Y1)] over the
  * n samples (X n x 12, Y and M n x 2) with respect to the master
  * parameters, ADDED to grad (PPM_MLP_PARAMS floats); the loss is added to
- * *loss.  Forward passes use the blob's BF16 weights. */
+ * *loss.  Forward passes use the blob's BF16 weights.  Deterministic: the
+ * sums of each 128-sample tile go to scratch memory allocated on the stream
+ * (at most about 5 MB) and are added in tile order, so equal inputs give
+ * bitwise equal grad and loss.  PPM_ENOMEM if the scratch cannot be had. */
 int ppm_mlp_grad(const void* blob, const float* X, const float* Y, const float* M, int64_t n,
                  float scale, float* grad, float* loss, void* stream);
 /* One Adam step (beta 0.9 / 0.999, eps 1e-8, step >= 1) on master with

@@ -25,7 +25,9 @@
 // (k_mlp_grad) is one thread per sample on the FP32 pipes: it needs the
 // activations of a 128-sample tile in shared memory for the weight
 // gradients anyway, stored feature-major with a row stride of 129 words so
-// the lanes of a warp always hit distinct banks.
+// the lanes of a warp always hit distinct banks.  Each tile's gradient goes
+// to scratch and k_mlp_grad_reduce adds the tiles in order (no floating
+// atomics), so a training run is bitwise reproducible.
 #include <cuda_bf16.h>
 
 #include "ppm_internal.cuh"
@@ -213,6 +215,7 @@ __device__ __forceinline__ float bf16_round(float v)
 }
 
 constexpr int kTile = 128;
+constexpr int kGradChunk = 256;     // tiles of partial gradients held at once (5.2 MB)
 constexpr int kLd = kTile + 1;        // row stride: lanes hit distinct banks
 
 struct GradSmem {
@@ -228,14 +231,14 @@ struct GradSmem {
 
 __global__ void __launch_bounds__(kTile)
 k_mlp_grad(const uint8_t* __restrict__ blob, const float* __restrict__ X, const float* __restrict__ Y,
-           const float* __restrict__ M, int64_t n, float scale, float* __restrict__ grad,
-           float* __restrict__ loss)
+           const float* __restrict__ M, int64_t n, int64_t tile0, float scale, float* __restrict__ part,
+           float* __restrict__ lpart)
 {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     GradSmem& sm = *reinterpret_cast<GradSmem*>(smem_raw);
     load_weights(sm.w, blob);
     const int s = threadIdx.x;
-    const int64_t gs = (int64_t)blockIdx.x * kTile + s;
+    const int64_t gs = (tile0 + blockIdx.x) * kTile + s;
     const bool live = gs < n;
     // forward, keeping the activations
     float x[kIn];
@@ -289,9 +292,9 @@ k_mlp_grad(const uint8_t* __restrict__ blob, const float* __restrict__ X, const 
     if (s == 0) {
         float t = 0.f;
         for (int q = 0; q < kTile / 32; ++q) t += sm.loss[q];
-        atomicAdd(loss, t);
+        lpart[blockIdx.x] = t;
     }
-    // weight gradients: sums over the tile's samples, one atomic per entry
+    // weight gradients: sums over the tile's samples, this tile's row of part
     for (int e = s; e < kParams; e += kTile) {
         float acc = 0.f;
         if (e < kW1) {
@@ -313,7 +316,25 @@ k_mlp_grad(const uint8_t* __restrict__ blob, const float* __restrict__ X, const 
             const int o = e - kW1 - kW2 - kW3 - 2 * kH;
             for (int q = 0; q < kTile; ++q) acc += sm.dout[o][q];
         }
-        atomicAdd(grad + e, acc);
+        part[(int64_t)blockIdx.x * kParams + e] = acc;
+    }
+}
+
+// the tiles' partial gradients and losses added to grad and loss in tile
+// order: equal inputs give bitwise equal results
+__global__ void k_mlp_grad_reduce(const float* __restrict__ part, const float* __restrict__ lpart, int ntiles,
+                                  float* __restrict__ grad, float* __restrict__ loss)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < kParams) {
+        float acc = 0.f;
+        for (int t = 0; t < ntiles; ++t) acc += part[(int64_t)t * kParams + e];
+        grad[e] += acc;
+    }
+    if (e == 0) {
+        float l = 0.f;
+        for (int t = 0; t < ntiles; ++t) l += lpart[t];
+        *loss += l;
     }
 }
 
@@ -504,10 +525,31 @@ int ppm_mlp_grad(const void* blob, const float* X, const float* Y, const float* 
         PPM_CUDA(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GradSmem)));
         attr_set[dev] = true;
     }
-    k_mlp_grad<<<(unsigned)((n + kTile - 1) / kTile), kTile, sizeof(GradSmem), (cudaStream_t)stream>>>(
-        (const uint8_t*)blob, X, Y, M, n, scale, grad, loss);
-    PPM_LAUNCH_CHECK();
-    return PPM_OK;
+    // per-tile partial sums in stream-ordered scratch, reduced in tile
+    // order, at most kGradChunk tiles at a time
+    const cudaStream_t st = (cudaStream_t)stream;
+    const int64_t ntiles = (n + kTile - 1) / kTile;
+    const int chunk = (int)(ntiles < kGradChunk ? ntiles : kGradChunk);
+    float* part = nullptr;
+    if (cudaMallocAsync((void**)&part, ((size_t)chunk * kParams + chunk) * sizeof(float), st) != cudaSuccess) {
+        cudaGetLastError();
+        return PPM_ENOMEM;
+    }
+    float* lpart = part + (size_t)chunk * kParams;
+    int rc = PPM_OK;
+    for (int64_t t0 = 0; t0 < ntiles && rc == PPM_OK; t0 += chunk) {
+        const int nt = (int)(ntiles - t0 < chunk ? ntiles - t0 : chunk);
+        k_mlp_grad<<<(unsigned)nt, kTile, sizeof(GradSmem), st>>>((const uint8_t*)blob, X, Y, M, n, t0, scale,
+                                                                   part, lpart);
+        k_mlp_grad_reduce<<<(kParams + 255) / 256, 256, 0, st>>>(part, lpart, nt, grad, loss);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            ppm_note_cuda_error(e, "launch", __FILE__, __LINE__);
+            rc = PPM_ECUDA;
+        }
+    }
+    cudaFreeAsync(part, st);
+    return rc;
 }
 
 int ppm_mlp_adam(float* master, float* grad, float* m, float* v, int32_t step, float lr, void* blob,

@@ -83,6 +83,41 @@ def test_gradient_matches_oracle():
     assert np.all(err <= 1e-3 * np.abs(ref) + 1e-5 * np.abs(ref).max()), float((err / (np.abs(ref) + 1e-12)).max())
 
 
+def test_gradient_over_several_chunks_is_deterministic():
+    """More tiles than one scratch chunk (256 tiles of 128) plus a ragged
+    tail: matches the oracle, and a second call gives the same bits."""
+    import torch
+    from paper_2504_04411_gb300 import ppm
+    master, X, Y, M = _random_net(5, n=256 * 128 + 77)
+    blob = _to_dev_blob(_host_blob(master))
+    Xd, Yd, Md = (torch.from_numpy(v).cuda() for v in (X, Y, M))
+    scale = 1.0 / X.shape[0]
+    out = []
+    for _ in range(2):
+        grad = torch.zeros(MO.N_PARAMS, device="cuda")
+        loss = torch.zeros(1, device="cuda")
+        ppm.ppm_mlp_grad(blob, Xd, Yd, Md, scale, grad, loss)
+        out.append((grad.cpu().numpy(), float(loss)))
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+    ref_loss, ref = MO.loss_and_grad(MO.from_blob(_host_blob(master)), X, Y, M, scale)
+    assert out[0][1] == pytest.approx(ref_loss, rel=1e-5)
+    err = np.abs(out[0][0].astype(np.float64) - ref)
+    assert np.all(err <= 1e-3 * np.abs(ref) + 1e-5 * np.abs(ref).max())
+
+
+def test_training_is_bitwise_reproducible():
+    import torch
+    from paper_2504_04411_gb300 import learned
+    rng = np.random.default_rng(6)
+    X = torch.from_numpy(rng.normal(0, 1, (9000, 12)).astype(np.float32)).cuda()
+    Y = torch.from_numpy(np.stack([np.tanh(X.cpu().numpy()[:, 1]), (X.cpu().numpy()[:, 2] > 0)], 1)
+                         .astype(np.float32)).cuda()
+    runs = [learned.train(X, Y, torch.ones_like(Y), epochs=3) for _ in range(2)]
+    assert torch.equal(runs[0][1], runs[1][1])
+    assert torch.equal(runs[0][0], runs[1][0])
+    assert runs[0][2] == runs[1][2]
+
+
 def test_pack_rounds_to_nearest_even():
     import torch
     from paper_2504_04411_gb300 import ppm
