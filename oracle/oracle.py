@@ -45,7 +45,7 @@ class _Params(ctypes.Structure):
                 ("r_min", ctypes.c_float), ("n_vm", ctypes.c_float),
                 ("alpha_f", ctypes.c_double), ("rgb_test", ctypes.c_int32),
                 ("vcm", ctypes.c_int32), ("i0", ctypes.c_int32),
-                ("pad", ctypes.c_int32)]
+                ("test", ctypes.c_int32)]
 
 
 _lib = None
@@ -63,6 +63,12 @@ def lib():
         _lib.oracle_f_cdf.argtypes = [d, d, d]
         _lib.oracle_f_crit.restype = d
         _lib.oracle_f_crit.argtypes = [d, d, d]
+        _lib.oracle_chi2_cdf.restype = d
+        _lib.oracle_chi2_cdf.argtypes = [d, d]
+        _lib.oracle_chi2_crit.restype = d
+        _lib.oracle_chi2_crit.argtypes = [d, d]
+        _lib.oracle_chi2_counts.restype = d
+        _lib.oracle_chi2_counts.argtypes = [i, P]
         _lib.oracle_anova_f.restype = d
         _lib.oracle_anova_f.argtypes = [i, d, P, P, P]
         _lib.oracle_normal_dot.restype = i
@@ -99,6 +105,22 @@ def f_crit(d1: float, d2: float, alpha: float) -> float:
 
 def betainc(a: float, b: float, x: float) -> float:
     return lib().oracle_betainc(a, b, x)
+
+
+# -- Sec. 3.2.3: CPPM's chi-square test of the counts -------------------------
+def chi2_cdf(k: float, x: float) -> float:
+    return lib().oracle_chi2_cdf(k, x)
+
+
+def chi2_crit(k: float, alpha: float) -> float:
+    """(1-alpha) quantile of chi^2(k): CPPM's critical value chi_c."""
+    return lib().oracle_chi2_crit(k, alpha)
+
+
+def chi2_counts(counts) -> float:
+    """Pearson's X^2 of the counts against an even spread."""
+    c = np.ascontiguousarray(counts, np.int64)
+    return lib().oracle_chi2_counts(len(c), _ptr(c))
 
 
 # -- Eq. (f-statistic) ------------------------------------------------------
@@ -159,7 +181,7 @@ class OracleResult:
 
 def run(hp: dict, photons: dict, r_init, iters: int, *, k=0.7, alpha=0.75,
         r_min=None, alpha_f=0.01, rgb_test=False, vcm=False, n_vm=None,
-        i0=1, outputs=True) -> OracleResult:
+        i0=1, test=0, outputs=True) -> OracleResult:
     """Run the method for ``iters`` iterations over brute-force all pairs.
 
     hp: dict with pos (nh,3), u (nh,3), v (nh,3) float32 and optional
@@ -167,6 +189,8 @@ def run(hp: dict, photons: dict, r_init, iters: int, *, k=0.7, alpha=0.75,
     photons: dict with pos (iters,J,3) float32, flux (iters,J) or
         (iters,J,3) float32, optional nq (iters,J) uint32, and for VCM+
         rho (iters,J,2) float32 and wq (iters,J) uint32.
+    test: 0 for the ANOVA F-test, 1 for CPPM's chi-square test of the
+        counts (then F holds X^2 and Fc holds chi_c).
     """
     pos = np.ascontiguousarray(hp["pos"], np.float32)
     nh = pos.shape[0]
@@ -191,7 +215,7 @@ def run(hp: dict, photons: dict, r_init, iters: int, *, k=0.7, alpha=0.75,
         r_min = 1e-3 * float(np.max(r_init)) if nh else 0.0
     prm = _Params(k=k, alpha=alpha, r_min=r_min,
                   n_vm=float(J if n_vm is None else n_vm), alpha_f=alpha_f,
-                  rgb_test=int(rgb_test), vcm=int(vcm), i0=i0, pad=0)
+                  rgb_test=int(rgb_test), vcm=int(vcm), i0=i0, test=int(test))
     if outputs:
         o_r = np.zeros((iters + 1, nh), np.float32)
         o_c = np.zeros((iters, nh, NG), np.int32)

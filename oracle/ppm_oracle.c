@@ -25,7 +25,11 @@
  * sample tables and against the exact value F=1 for a single nonzero sample;
  * classification against FP64 atan2 geometry and brute-force area fractions;
  * the estimate against the analytic constant-irradiance plane; the rejection
- * rate against alpha_F; the radius update against Eq. (radiusupdate).
+ * rate against alpha_F; the radius update against Eq. (radiusupdate).  The
+ * chi-square test of CPPM: its critical value against the closed form
+ * -2 ln(alpha) of two degrees of freedom, the 24.724 printed in Sec. 6.1.1
+ * and scipy; the statistic against scipy.stats.chisquare; its rejection rate
+ * against alpha; its blindness to a zero-flux shadow edge (Sec. 3.2.3).
  */
 #include <math.h>
 #include <stdint.h>
@@ -125,6 +129,60 @@ double oracle_f_crit(double d1, double d2, double alpha)
         if (oracle_f_cdf(d1, d2, mid) < target) lo = mid; else hi = mid;
     }
     return 0.5 * (lo + hi);
+}
+
+/* ------------------------------------------------------------------------
+ * 1b. The chi-square test that CPPM uses (Sec. 3.2.3; settings in Sec.
+ *     6.1.1): are the in-disk photons spread evenly over the n equi-areal
+ *     groups?  It looks at the counts c_g only, not at what the photons
+ *     carry.  Statistic: Pearson's X^2 = sum_g (c_g - E)^2 / E with
+ *     E = C / n and C = sum_g c_g; a disk without photons gives X^2 = 0 (no
+ *     evidence against uniformity).  Critical value chi_c: the (1 - alpha)
+ *     quantile of chi^2(n - 1), whose CDF is P(k/2, x/2) with P the
+ *     regularized lower incomplete gamma function.  P comes from its power
+ *     series
+ *         P(a, z) = z^a e^-z / Gamma(a + 1) * sum_{j >= 0} z^j / ((a+1)...(a+j)),
+ *     whose terms are all positive (no cancellation), summed in binary128.
+ *     The quantile is found by plain bisection on the CDF.
+ * ---------------------------------------------------------------------- */
+double oracle_chi2_cdf(double k, double x)
+{
+    if (x <= 0.0) return 0.0;
+    const or_quad a = (or_quad)k / 2, z = (or_quad)x / 2;
+    or_quad term = 1, sum = 1;
+    for (int j = 1; j < 100000; ++j) {
+        term *= z / (a + j);
+        sum += term;
+        if (term < sum * (or_quad)1e-33) break;
+    }
+    const or_quad lp = a * OR_LOG(z) - z - OR_LGAMMA(a + 1) + OR_LOG(sum);
+    return (double)OR_EXP(lp);
+}
+
+double oracle_chi2_crit(double k, double alpha)
+{
+    double target = 1.0 - alpha, lo = 0.0, hi = 1.0;
+    while (oracle_chi2_cdf(k, hi) < target) { lo = hi; hi *= 2.0; }
+    for (int it = 0; it < 2000; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (oracle_chi2_cdf(k, mid) < target) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+double oracle_chi2_counts(int n, const int64_t* counts)
+{
+    int64_t C = 0;
+    for (int g = 0; g < n; ++g) C += counts[g];
+    if (C == 0) return 0.0;
+    const double E = (double)C / n;
+    double x2 = 0.0;
+    for (int g = 0; g < n; ++g) {
+        const double d = (double)counts[g] - E;
+        x2 += d * d / E;
+    }
+    return x2;
 }
 
 /* ------------------------------------------------------------------------
@@ -269,7 +327,8 @@ static double or_lum(double R, double G, double B)
  *      c. tau_h += sum(w * Phi) / (pi r^2) with the radius of this iteration;
  *      d. m = t' J with t' = t+1 iterations in the window; two-pass ANOVA F
  *         per tested channel; F_c from d2 = 12 (m - 1); reject iff F > F_c
- *         (any channel in RGB mode);
+ *         (any channel in RGB mode).  With test = 1 (CPPM) instead: reject
+ *         iff Pearson's X^2 of the window's counts exceeds chi_c;
  *      e. reject: shrink r, clear the window, t = 0; else t = t'.
  *    Hit points are independent given the photons, so the loop over hit
  *    points is a plain parallel-for.
@@ -283,7 +342,8 @@ typedef struct {
     int32_t rgb_test; /* 1: F-test on R, G and B, reject if any rejects */
     int32_t vcm;      /* 1: weight each sample by the VCM+ merge weight */
     int32_t i0;       /* global index of the first iteration (1-based) */
-    int32_t pad;
+    int32_t test;     /* 0: ANOVA F-test (FPPM); 1: chi-square test of the
+                         window's counts (CPPM, Sec. 3.2.3) decides alone */
 } oracle_params;
 
 typedef struct {
@@ -369,7 +429,8 @@ int oracle_run(int64_t nh, const float* hp_pos, const float* hp_u,
                uint8_t* out_reject, int32_t* out_pairs, int32_t* out_t,
                double* out_tau)
 {
-    if (nh < 0 || iters < 0 || J < 2 || (nch != 1 && nch != 3) || !prm)
+    if (nh < 0 || iters < 0 || J < 2 || (nch != 1 && nch != 3) || !prm ||
+        (prm->test != 0 && prm->test != 1))
         return -1;
     if (prm->vcm && (!hp_rho || !ph_rho || !ph_wq || !hp_nq)) return -1;
     const int use_normals = (hp_nq != NULL && ph_nq != NULL);
@@ -381,6 +442,7 @@ int oracle_run(int64_t nh, const float* hp_pos, const float* hp_u,
     double* fc = (double*)malloc(sizeof(double) * (size_t)(tmax + 1));
     for (int t = 1; t <= tmax; ++t)
         fc[t] = oracle_f_crit(OR_NG - 1, OR_NG * ((double)t * (double)J - 1.0), prm->alpha_f);
+    const double chic = prm->test == 1 ? oracle_chi2_crit(OR_NG - 1, prm->alpha_f) : 0.0;
     float* bound = (float*)malloc(sizeof(float) * (size_t)(iters > 0 ? iters : 1));
     for (int it = 0; it < iters; ++it)
         bound[it] = oracle_radius_bound(prm->r_min, prm->alpha, prm->i0 + it);
@@ -442,12 +504,18 @@ int oracle_run(int64_t nh, const float* hp_pos, const float* hp_u,
                 if (ch == 0) F0 = F;
                 if (F > fc[tp]) reject = 1;
             }
+            if (prm->test == 1) {
+                /* CPPM: the count test alone decides; its statistic takes
+                 * F's place in the outputs */
+                F0 = oracle_chi2_counts(OR_NG, cnt);
+                reject = F0 > chic;
+            }
             size_t o = (size_t)it * nh + h;
             if (out_counts) for (int g = 0; g < OR_NG; ++g) out_counts[o * OR_NG + g] = (int32_t)cnt[g];
             if (out_S) for (int g = 0; g < OR_NG; ++g) out_S[o * OR_NG + g] = S[g];
             if (out_Q) for (int g = 0; g < OR_NG; ++g) out_Q[o * OR_NG + g] = Q[g];
             if (out_F) out_F[o] = F0;
-            if (out_Fc) out_Fc[o] = fc[tp];
+            if (out_Fc) out_Fc[o] = prm->test == 1 ? chic : fc[tp];
             if (out_reject) out_reject[o] = (uint8_t)reject;
             if (out_pairs) out_pairs[o] = pairs;
             if (reject) {

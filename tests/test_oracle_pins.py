@@ -131,6 +131,76 @@ def test_anova_equal_flux_limit_is_pearson_chi2():
     assert 11 * O.anova_f(groups, 1e12) == pytest.approx(chi2, rel=1e-8)
 
 
+# ---------------------------------------------- CPPM's chi-square test ------
+@pytest.mark.parametrize("alpha", [0.5, 0.1, 0.05, 0.01, 1e-4])
+def test_chi2_crit_two_dof_closed_form(alpha):
+    # chi^2(2) is the exponential law with mean 2: quantile -2 ln(alpha)
+    assert O.chi2_crit(2, alpha) == pytest.approx(-2.0 * math.log(alpha), rel=1e-12)
+
+
+def test_chi2_crit_paper_value_and_scipy():
+    # Sec. 6.1.1 prints chi_c = 24.724 for CPPM's 12 groups at alpha 0.01
+    want = GOLD["chi_c"]["value"]
+    got = O.chi2_crit(NG - 1, ALPHA)
+    assert abs(got - want) < 10.0 ** -GOLD["chi_c"]["digits"], got
+    for k in (1, 3, 11, 40):
+        for a in (0.2, 0.01, 1e-3):
+            assert O.chi2_crit(k, a) == pytest.approx(stats.chi2.ppf(1 - a, k), rel=1e-11)
+
+
+def test_chi2_counts_matches_scipy_and_limits():
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        c = rng.integers(0, 50, NG)
+        if c.sum() == 0:
+            continue
+        assert O.chi2_counts(c) == pytest.approx(stats.chisquare(c).statistic, rel=1e-12)
+    assert O.chi2_counts(np.full(NG, 9)) == 0.0                 # even spread
+    one = np.zeros(NG, np.int64)
+    one[5] = 40
+    assert O.chi2_counts(one) == pytest.approx((NG - 1) * 40, rel=1e-14)   # all in one group: (n-1) C
+    assert O.chi2_counts(np.zeros(NG, np.int64)) == 0.0         # no photons: no evidence
+
+
+def test_cppm_rejection_rate_is_alpha():
+    # under an even spread of photons, Pearson's X^2 of the counts follows
+    # chi^2(11) closely (about nine photons per group here), so CPPM's first
+    # test rejects with probability about alpha
+    J, r0, seeds = 20000, 0.045, 10
+    rej = n = 0
+    for s in range(seeds):
+        sc = synth.PlaneScene(nside=64, J=J, r0=r0, step=False, lo=-r0, hi=1 + r0,
+                              seed=synth.SEED_BASE + 100 + s)
+        hp = sc.hitpoints().numpy()
+        res = O.run(hp, synth.stack_numpy([sc.photons(1)]), r0, 1, test=1)
+        assert np.allclose(res.Fc, O.chi2_crit(NG - 1, ALPHA))
+        rej += int(res.reject[0].sum())
+        n += res.reject[0].size
+    p = rej / n
+    sigma = math.sqrt(ALPHA * (1 - ALPHA) / n)
+    assert abs(p - ALPHA) < 5 * sigma, (p, sigma)
+
+
+def test_cppm_is_blind_to_a_zero_flux_edge():
+    # Sec. 3.2.3: the chi-square test sees where photons land, not what they
+    # carry.  Photons keep landing evenly in a shadow (flux 0 for x > 0.5),
+    # so CPPM keeps the radii at the edge that the F-test shrinks.
+    sc = synth.PlaneScene(nside=32, J=20000, r0=0.04, step=True)
+    hp = sc.hitpoints().numpy()
+    iters = 10
+    ph = synth.stack_numpy([sc.photons(i) for i in range(1, iters + 1)])
+    f = O.run(hp, ph, sc.r0, iters)
+    c = O.run(hp, ph, sc.r0, iters, test=1)
+    x, y = hp["pos"][:, 0], hp["pos"][:, 1]
+    near = (np.abs(x - 0.5) < 0.5 * sc.r0) & (y > 2 * sc.r0) & (y < 1 - 2 * sc.r0)
+    assert np.all(f.r[-1][near] < sc.r0)
+    assert np.mean(c.r[-1][near] < sc.r0) < 0.3
+    # both take the same pairs and windows until their decisions differ
+    assert np.array_equal(f.pairs[0], c.pairs[0]) and np.array_equal(f.counts[0], c.counts[0])
+    for it in range(iters):
+        assert np.allclose(c.F[it], [O.chi2_counts(k) for k in c.counts[it]], rtol=1e-12)
+
+
 # ------------------------------------------------------ classification ------
 def _geom_group(xh, u, v, r, xp):
     d = np.asarray(xh, float) - np.asarray(xp, float)
