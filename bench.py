@@ -179,7 +179,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="frame", choices=["frame", "tiny", "batched", "learned", "vcm"])
+    ap.add_argument("--config", default="frame", choices=["frame", "tiny", "batched", "learned", "vcm", "cppm"])
     ap.add_argument("--mapping", type=int, default=None, help="skip the autotuner: traversal")
     ap.add_argument("--cell-factor", type=float, default=None, help="skip the autotuner: cell factor")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -187,7 +187,7 @@ def parse():
     ap.add_argument("--no-flush", action="store_true")
     a = ap.parse_args()
     if a.steps is None:
-        a.steps = 16 if a.config in ("batched", "vcm") else (64 if a.config == "learned" else 64 - a.warmup)
+        a.steps = 16 if a.config in ("batched", "vcm") else (64 if a.config in ("learned", "cppm") else 64 - a.warmup)
     return a
 
 
@@ -259,6 +259,8 @@ def main():
         line = run_batched(args, rank, world, local, dist)
     elif args.config == "learned":
         line = run_learned(args, rank, world, local, dist)
+    elif args.config == "cppm":
+        line = run_cppm(args, rank, world, local, dist)
     else:
         line = run_single(args, rank, world, local, dist)
     if rank == 0:
@@ -570,6 +572,64 @@ def run_learned(args, rank, world, local, dist):
                          "seconds": train_s}}
 
 
+def run_cppm(args, rank, world, local, dist):
+    """The paper's F-test (FPPM) against CPPM's chi-square test of the
+    counts (Sec. 3.2.3, compared in Sec. 6.1.1) on the frame-sized scene,
+    both through the library with the same photons: MSE against the scene's
+    closed-form irradiance at equal iterations, and the iterations each
+    needs to reach the other's final MSE.  The metric is the CPPM run's
+    pair-test rate (device time of grid build + gather per iteration)."""
+    import torch
+
+    from paper_2504_04411_gb300 import learned, ppm
+    N = args.steps if args.steps else 64
+    sc, desc = make_scene("frame", rank)
+    hp = sc.hitpoints("cuda")
+    ref = sc.irradiance(hp).to("cuda", torch.float32)
+    stream = torch.cuda.current_stream()
+
+    def timed(test):
+        p = ppm.ppm_default_params()
+        p.test = test
+        p.mapping = args.mapping if args.mapping is not None else 0
+        p.cell_factor = args.cell_factor if args.cell_factor is not None else 0.6
+        est = ppm.Estimator(hp, sc.r0, 0.75, p)
+        ms, mse, pairs, rejects = [], [], 0, 0
+        for i in range(1, N + 1):
+            ph = sc.photons(i, "cuda")
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            est.step(ph)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+            mse.append(float(((est.radiance() - ref) ** 2).mean()))
+            s = est.stats()
+            pairs += s.pairs
+            rejects += s.rejects
+        r = est.state()["r"]
+        est.close()
+        return ms, mse, pairs, rejects, float(r.mean()) / sc.r0
+
+    fms, fmse, fpairs, frej, fr = timed(0)
+    cms, cmse, cpairs, crej, cr = timed(1)
+    c_reach = learned.iterations_to_reach(cmse, fmse[-1])
+    f_reach = learned.iterations_to_reach(fmse, cmse[-1])
+    at = {k: {"fppm": fmse[k - 1], "cppm": cmse[k - 1]} for k in (8, 16, 32, 64) if k <= N}
+    return {"metric": METRIC, "value": cpairs / (sum(cms) / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": N, "warmup": 0, "ms_per_step": sum(cms) / N, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(desc, workload="FPPM vs CPPM: " + desc["workload"], l2="not flushed",
+                           parallelism="single GPU", mapping=0, cell_factor=0.6),
+            "fppm_vs_cppm": {"mse_at": at, "fppm_final_mse": fmse[-1], "cppm_final_mse": cmse[-1],
+                             "cppm_iterations_to_fppm_final": c_reach,
+                             "fppm_iterations_to_cppm_final": f_reach,
+                             "rejects_total": {"fppm": frej, "cppm": crej},
+                             "mean_final_radius_over_r0": {"fppm": fr, "cppm": cr},
+                             "ms_per_iteration": {"fppm": sum(fms) / N, "cppm": sum(cms) / N},
+                             "pairs_per_s": {"fppm": fpairs / (sum(fms) / 1e3), "cppm": cpairs / (sum(cms) / 1e3)}}}
+
+
 def run_reference(args):
     """The oracle as it stands on the host cores, on the same config, one
     bounded sample of hit points per step against the step's photons."""
@@ -583,7 +643,7 @@ def run_reference(args):
     threads = os.cpu_count() or 1
     os.environ.setdefault("OMP_NUM_THREADS", str(threads))
     W, K = args.warmup, args.steps
-    kw = {"vcm": True, "k": 0.9} if args.config == "vcm" else {}
+    kw = {"vcm": True, "k": 0.9} if args.config == "vcm" else ({"test": 1} if args.config == "cppm" else {})
     ph_np = synth.stack_numpy([sc.photons(1, "cpu")])
     _, dt = oracle_sample(sc, ph_np, hp_np, 64, seed=0, **kw)
     per_step_s = min(2.0, 150.0 / (W + K))

@@ -111,7 +111,19 @@ typedef struct {
     int32_t tile;       /* batches: hit points per tile of the persistent
                            gather, a multiple of 64 in [64, 1024]; 0 = 64.
                            Contexts ignore it.  Results do not depend on it. */
-    int32_t reserved[5];
+    int32_t test;       /* 0: the ANOVA F-test of the paper (FPPM, default);
+                           1: CPPM's chi-square test (Sec. 3.2.3, settings of
+                           Sec. 6.1.1): reject iff Pearson's X^2 of the
+                           window's in-disk counts c_g over the 12 equal-area
+                           groups exceeds chi_c, the (1 - alpha_f) quantile of
+                           chi^2(11) (24.725 at alpha_f = 0.01).  The counts
+                           alone decide, not the flux.  X^2 is computed from
+                           exact integers, (12 sum c_g^2 - C^2) / C with
+                           C = sum c_g (0 when C = 0), and is what the F
+                           array of ppm_get_state then holds.  Contexts only
+                           (batches: PPM_EINVAL); not with rgb_test, features
+                           or the proposer (PPM_EINVAL); traversal 0. */
+    int32_t reserved[4];
 } ppm_params;
 
 /* Per-iteration counters of the last ppm_gather_test_update. */
@@ -216,6 +228,11 @@ int ppm_stats_host(ppm_ctx* ctx, int32_t iter, ppm_iter_stats* out);
  * (1 - alpha_f) quantile of F(11, 12 (t J - 1)) for t = 1 .. t_max, FP64,
  * out[0] = 0.  out: device array of t_max + 1 doubles.  Enqueued on stream. */
 int ppm_f_critical(int64_t J, double alpha_f, int32_t t_max, double* out, void* stream);
+
+/* Chi-square critical value on its own (the count test of CPPM, Sec. 3.2.3):
+ * out[0] = the (1 - alpha) quantile of chi^2(dof), FP64, dof in [1, 1000].
+ * out: device array of one double.  Enqueued on stream. */
+int ppm_chi2_critical(int32_t dof, double alpha, double* out, void* stream);
 
 /* Stable LSD radix sort of (key, value) pairs on the low `bits` bits of the
  * keys (1..32), the sort that orders photons by grid bucket in

@@ -194,7 +194,8 @@ int ensure_fc(ppm_ctx* c, int upto, int* launches)
     }
     // fill up to the capacity in one launch: later iterations hit the table
     const int to = c->fc_cap;
-    int rc = ppm_fcrit_fill(c->fc, c->fc_upto + 1, to, (double)c->J, c->prm.alpha_f, c->stream);
+    int rc = c->prm.test ? ppm_chi2_fill(c->fc, c->fc_upto + 1, to, PPM_NG - 1, c->prm.alpha_f, c->stream)
+                         : ppm_fcrit_fill(c->fc, c->fc_upto + 1, to, (double)c->J, c->prm.alpha_f, c->stream);
     if (rc) return rc;
     c->fc_upto = to;
     return PPM_OK;
@@ -311,6 +312,8 @@ int ppm_create(const ppm_hitpoints* hp, float r0, float alpha, const ppm_params*
     if (prm.vcm && hp->n > 0 && (!hp->rho || !hp->nq)) return PPM_EINVAL;
     if (prm.n_vm < 0.f) return PPM_EINVAL;
     if (prm.mapping < 0 || prm.mapping > 4) return PPM_EINVAL;
+    if (prm.test != 0 && prm.test != 1) return PPM_EINVAL;
+    if (prm.test && prm.rgb_test) return PPM_EINVAL;   // the count test has one statistic
 
     ppm_ctx* c = new (std::nothrow) ppm_ctx();
     if (!c) return PPM_ENOMEM;
@@ -634,6 +637,13 @@ int ppm_f_critical(int64_t J, double alpha_f, int32_t t_max, double* out, void* 
     cudaStream_t st = (cudaStream_t)stream;
     PPM_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
     return ppm_fcrit_fill(out, 1, t_max, (double)J, alpha_f, st);
+}
+
+int ppm_chi2_critical(int32_t dof, double alpha, double* out, void* stream)
+{
+    PPM_ENTRY();
+    if (dof < 1 || dof > 1000 || !(alpha > 0.0 && alpha < 1.0) || !out) return PPM_EINVAL;
+    return ppm_chi2_fill(out, 0, 0, (double)dof, alpha, (cudaStream_t)stream);
 }
 
 int ppm_sort_pairs(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,

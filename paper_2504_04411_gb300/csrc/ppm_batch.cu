@@ -510,6 +510,7 @@ int ppm_batch_create(int32_t n_problems, const ppm_hitpoints* hp, const float* r
     if (prm.channels != 1 && prm.channels != 3) return PPM_EINVAL;
     if (prm.rgb_test && prm.channels != 3) return PPM_EINVAL;
     if (prm.mapping < 0 || prm.mapping > 4 || prm.n_vm < 0.f) return PPM_EINVAL;
+    if (prm.test != 0) return PPM_EINVAL;   // the count test runs in contexts only
     if (prm.tile < 0 || prm.tile > 1024 || prm.tile % kThreads != 0) return PPM_EINVAL;
     const int64_t tile_hits = prm.tile > 0 ? prm.tile : kThreads;
     const int P = n_problems;

@@ -1,4 +1,5 @@
-// ppm_fcrit.cu -- table of F-test critical values, FP64 on the GPU.
+// ppm_fcrit.cu -- table of F-test critical values, FP64 on the GPU (and
+// the chi-square critical value of CPPM's count test, Sec. 3.2.3).
 //
 // Sec. 3.2.2: reject the null hypothesis iff F > F_c, where F_c is the
 // (1 - alpha_F) quantile of the F distribution with d1 = n - 1 = 11 and
@@ -110,7 +111,82 @@ __global__ void k_fcrit_table(double* __restrict__ table, int t_from, int t_to,
     table[t] = f_quantile(d1, d2, 1.0 - alpha);
 }
 
+// CPPM's count test (Sec. 3.2.3): chi_c = the (1 - alpha) quantile of
+// chi^2(k) with k = n - 1 = 11, whose CDF is P(k/2, x/2), P the regularized
+// lower incomplete gamma function: its power series below x = a + 1 and the
+// continued fraction of Q = 1 - P (modified Lentz) above (Press et al.,
+// Numerical Recipes, Sec. 6.2).
+__device__ double gamma_p_fp64(double a, double x)
+{
+    if (x <= 0.0) return 0.0;
+    const double lead = a * log(x) - x - lgamma(a);
+    if (x < a + 1.0) {
+        double ap = a, del = 1.0 / a, sum = del;
+        for (int n = 0; n < 4000; ++n) {
+            ap += 1.0;
+            del *= x / ap;
+            sum += del;
+            if (fabs(del) < fabs(sum) * 1e-17) break;
+        }
+        return sum * exp(lead);
+    }
+    const double tiny = 1e-300;
+    double b = x + 1.0 - a, c = 1.0 / tiny, d = 1.0 / b, h = d;
+    for (int i = 1; i < 4000; ++i) {
+        const double an = -i * (i - a);
+        b += 2.0;
+        d = an * d + b; if (fabs(d) < tiny) d = tiny;
+        c = b + an / c; if (fabs(c) < tiny) c = tiny;
+        d = 1.0 / d;
+        const double del = d * c;
+        h *= del;
+        if (fabs(del - 1.0) < 1e-16) break;
+    }
+    return 1.0 - exp(lead) * h;
+}
+
+// quantile of chi^2(k) at q: Newton on the CDF (derivative = the density
+// x^(a-1) e^(-x/2) / (2^a Gamma(a)), a = k/2) inside a bisection bracket
+__device__ double chi2_quantile(double k, double q)
+{
+    const double a = 0.5 * k;
+    double lo = 0.0, hi = k + 16.0;
+    for (int i = 0; i < 2000 && gamma_p_fp64(a, 0.5 * hi) < q; ++i) {
+        lo = hi;
+        hi *= 2.0;
+    }
+    double x = 0.5 * (lo + hi);
+    for (int it = 0; it < 200; ++it) {
+        const double g = gamma_p_fp64(a, 0.5 * x) - q;
+        if (g < 0.0) lo = x; else hi = x;
+        const double pdf = exp((a - 1.0) * log(x) - 0.5 * x - a * 0.6931471805599453 - lgamma(a));
+        double xn = pdf > 0.0 ? x - g / pdf : 0.5 * (lo + hi);
+        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+        if (fabs(xn - x) <= 1e-15 * x || hi - lo <= 1e-15 * hi) { x = xn; break; }
+        x = xn;
+    }
+    return x;
+}
+
+// every entry t_from .. t_to of the table gets chi_c: the count test's
+// critical value does not depend on the window length
+__global__ void k_chi2_table(double* __restrict__ table, int t_from, int t_to, double k, double alpha)
+{
+    const int t = t_from + blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > t_to) return;
+    table[t] = chi2_quantile(k, 1.0 - alpha);
+}
+
 }  // namespace
+
+int ppm_chi2_fill(double* table, int t_from, int t_to, double k, double alpha, cudaStream_t st)
+{
+    if (t_to < t_from) return PPM_OK;
+    const int n = t_to - t_from + 1;
+    k_chi2_table<<<(n + 63) / 64, 64, 0, st>>>(table, t_from, t_to, k, alpha);
+    PPM_LAUNCH_CHECK();
+    return PPM_OK;
+}
 
 int ppm_fcrit_fill(double* table, int t_from, int t_to, double J, double alpha, cudaStream_t st)
 {

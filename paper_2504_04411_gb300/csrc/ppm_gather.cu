@@ -44,7 +44,9 @@
 //      sums, and a shuffle reduce-scatter gathers the 36 group sums into
 //      the hit point's slots; one flux channel (otherwise it runs as 0).
 // A context that writes the proposer's features always runs traversal 0,
-// compiled separately so the other kernels carry none of that code.
+// compiled separately so the other kernels carry none of that code; so does
+// a context whose radii follow CPPM's chi-square test of the counts
+// (ppm_params.test = 1) instead of the F-test.
 #include "ppm_gather_impl.cuh"
 
 namespace {
@@ -70,7 +72,10 @@ int launch_gather(ppm_ctx* c, const GatherArgs& a, const Prob& pr)
 {
     const unsigned nb = (unsigned)((c->nh + kThreads - 1) / kThreads);
     const int m = c->prm.mapping;
-    if (a.feat)   // features: traversal 0 (results do not depend on the traversal)
+    if (c->prm.test) {   // CPPM's count test: traversal 0, one tested channel
+        if constexpr (NTC == 1)
+            k_gather_update<NCH, 1, NORMALS, VCM, 0, false, true><<<nb, kThreads, 0, c->stream>>>(a, pr);
+    } else if (a.feat)   // features: traversal 0 (results do not depend on the traversal)
         k_gather_update<NCH, NTC, NORMALS, VCM, 0, true><<<nb, kThreads, 0, c->stream>>>(a, pr);
     else if (m == 1)
         k_gather_update<NCH, NTC, NORMALS, VCM, 1><<<nb, kThreads, 0, c->stream>>>(a, pr);

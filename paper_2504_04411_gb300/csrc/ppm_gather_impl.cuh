@@ -614,8 +614,10 @@ __device__ __forceinline__ void gather_warp_hit(const GatherArgs& a, const Hit& 
 
 // FEAT: also write the proposer's features (a separate instantiation: the
 // call alone costs the feature-free kernel about 10% through register
-// allocation in the cell walk)
-template <int NCH, int NTC, bool NORMALS, bool VCM, int MAPPING, bool BATCH, bool FEAT = false>
+// allocation in the cell walk).  CHI2: CPPM's count test decides instead of
+// the F-test (its own instantiation too).
+template <int NCH, int NTC, bool NORMALS, bool VCM, int MAPPING, bool BATCH, bool FEAT = false,
+          bool CHI2 = false>
 __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr, int64_t h0,
                                              int64_t h_end, BlockShared<NCH, NTC, MAPPING>& bsh)
 {
@@ -883,6 +885,21 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
         const int64_t nh = a.nh;
         bool reject = false;
         float F0 = 0.f;
+        // CPPM (Sec. 3.2.3): Pearson's X^2 of the window's in-disk counts
+        // against an even spread, from exact integers:
+        // X^2 = (12 sum_g c_g^2 - C^2) / C, C = sum_g c_g (0 without photons)
+        double x2 = 0.0;
+        if constexpr (CHI2) {
+            unsigned long long C = 0ull, C2 = 0ull;
+#pragma unroll
+            for (int g = 0; g < PPM_NG; ++g) {
+                const unsigned long long cg = (unsigned long long)a.cnt[g * nh + h] + gs.C(g);
+                C += cg;
+                C2 += cg * cg;
+            }
+            if (C > 0ull) x2 = (double)(PPM_NG * C2 - C * C) / (double)C;
+            reject = x2 > pr.fc[tpi];
+        }
 #pragma unroll
         for (int c = 0; c < NTC; ++c) {
             float Sg[PPM_NG];
@@ -904,8 +921,8 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
             const float ssw = Qsum - S2 / m;
             float F = 0.f;
             if (ssw > 0.f) F = (dev2 / ssw) * (((float)PPM_NG * (m - 1.0f)) / ((float)(PPM_NG - 1) * m));
-            if (c == 0) F0 = F;
-            if (ssw > 0.f && (double)F > pr.fc[tpi]) reject = true;
+            if (c == 0) F0 = CHI2 ? (float)x2 : F;
+            if (!CHI2 && ssw > 0.f && (double)F > pr.fc[tpi]) reject = true;
             if constexpr (FEAT)
                 if (c == 0) write_features<NCH, NTC, MAPPING>(a, pr, gs, h, Sg, Ssum, dev2, F, (float)pr.fc[tpi], r, tp);
         }
@@ -986,13 +1003,13 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
 }
 
 // one context: one block per kThreads hit points
-template <int NCH, int NTC, bool NORMALS, bool VCM, int MAPPING, bool FEAT = false>
+template <int NCH, int NTC, bool NORMALS, bool VCM, int MAPPING, bool FEAT = false, bool CHI2 = false>
 __global__ void __launch_bounds__(kThreads, kMinBlocks<MAPPING, NTC>)
 k_gather_update(GatherArgs a, Prob pr)
 {
     __shared__ BlockShared<NCH, NTC, MAPPING> bsh;
     const int64_t h0 = (int64_t)blockIdx.x * kThreads;
-    gather_block<NCH, NTC, NORMALS, VCM, MAPPING, false, FEAT>(a, pr, h0, a.nh, bsh);
+    gather_block<NCH, NTC, NORMALS, VCM, MAPPING, false, FEAT, CHI2>(a, pr, h0, a.nh, bsh);
 }
 
 }  // namespace

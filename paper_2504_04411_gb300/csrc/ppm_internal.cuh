@@ -123,6 +123,8 @@ int ppm_exclusive_scan_u32(uint32_t* data, int64_t n, uint32_t* partials,
 // ---------------------------------------------------------------------------
 int ppm_fcrit_fill(double* table, int t_from, int t_to, double J, double alpha,
                    cudaStream_t st);
+// every entry t_from .. t_to = the (1 - alpha) quantile of chi^2(k)
+int ppm_chi2_fill(double* table, int t_from, int t_to, double k, double alpha, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Context

@@ -456,6 +456,7 @@ int ppm_set_features(ppm_ctx* c, int32_t enable)
 {
     PPM_ENTRY();
     if (!c) return PPM_EINVAL;
+    if (enable && c->prm.test) return PPM_EINVAL;   // features describe the F-test's window
     if (!enable) {
         if (c->mlp) return PPM_ESTATE;          // the proposer reads the features
         PPM_CUDA(cudaStreamSynchronize(c->stream));

@@ -38,7 +38,8 @@ class ppm_params(ctypes.Structure):
                 ("rmin_ratio", ctypes.c_float), ("cell_factor", ctypes.c_float),
                 ("channels", ctypes.c_int32), ("rgb_test", ctypes.c_int32),
                 ("vcm", ctypes.c_int32), ("n_vm", ctypes.c_float),
-                ("mapping", ctypes.c_int32), ("tile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("mapping", ctypes.c_int32), ("tile", ctypes.c_int32), ("test", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class ppm_iter_stats(ctypes.Structure):
@@ -58,7 +59,7 @@ class ppm_state_view(ctypes.Structure):
 # every symbol include/ppm.h declares
 EXPORTS = ("ppm_default_params", "ppm_create", "ppm_set_stream", "ppm_build_grid",
            "ppm_gather_test_update", "ppm_radiance", "ppm_get_state", "ppm_set_state",
-           "ppm_set_iteration", "ppm_stats", "ppm_f_critical", "ppm_sort_pairs",
+           "ppm_set_iteration", "ppm_stats", "ppm_f_critical", "ppm_chi2_critical", "ppm_sort_pairs",
            "ppm_destroy", "ppm_strerror", "ppm_sort_pairs_noalloc",
            "ppm_batch_create", "ppm_batch_iterate", "ppm_batch_radiance",
            "ppm_batch_get_state", "ppm_batch_stats", "ppm_batch_graph_ready",
@@ -104,6 +105,8 @@ def load(path: str = LIB_PATH):
     L.ppm_stats_host.argtypes = [c_p, ctypes.c_int32, ctypes.POINTER(ppm_iter_stats)]
     L.ppm_f_critical.restype = ctypes.c_int
     L.ppm_f_critical.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_int32, c_p, c_p]
+    L.ppm_chi2_critical.restype = ctypes.c_int
+    L.ppm_chi2_critical.argtypes = [ctypes.c_int32, ctypes.c_double, c_p, c_p]
     L.ppm_sort_pairs.restype = ctypes.c_int
     L.ppm_sort_pairs.argtypes = [c_p, c_p, c_p, c_p, ctypes.c_int64, ctypes.c_int32, c_p]
     L.ppm_sort_pairs_noalloc.restype = ctypes.c_int
@@ -260,6 +263,10 @@ def ppm_stats_host(ctx, it: int) -> ppm_iter_stats:
 
 def ppm_f_critical(J: int, alpha_f: float, t_max: int, out, stream=None) -> None:
     _check("ppm_f_critical", load().ppm_f_critical(J, alpha_f, t_max, _ptr(out), _stream(stream)))
+
+
+def ppm_chi2_critical(dof: int, alpha: float, out, stream=None) -> None:
+    _check("ppm_chi2_critical", load().ppm_chi2_critical(dof, alpha, _ptr(out), _stream(stream)))
 
 
 def ppm_sort_pairs(keys_in, vals_in, keys_out, vals_out, bits: int, stream=None) -> None:

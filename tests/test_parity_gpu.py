@@ -56,6 +56,87 @@ def test_fcrit_other_alpha_and_monotone():
             assert got[t] == pytest.approx(O.f_crit(11, 12 * (t * 5000 - 1), a), rel=1e-11)
 
 
+# ----------------------------------------------- CPPM's chi-square test ----
+@pytest.mark.parametrize("dof", [1, 2, 11, 40])
+def test_chi2_critical_matches_oracle(dof):
+    import torch
+    from paper_2504_04411_gb300 import ppm
+    out = torch.empty(1, device="cuda", dtype=torch.float64)
+    for a in (0.2, 0.01, 1e-3):
+        ppm.ppm_chi2_critical(dof, a, out)
+        assert float(out) == pytest.approx(O.chi2_crit(dof, a), rel=1e-12), (dof, a)
+
+
+def _cppm_check(states, stats, L, ref, iters):
+    """Decisions from exact integer counts: identical on both sides, so the
+    whole trajectory must agree (no band, no divergence)."""
+    rep = compare(states, stats, L, ref, iters)
+    assert rep.diverged == 0 and not rep.band_flips, rep
+    for it in range(iters):
+        assert np.array_equal(states[it]["t"] == 0, ref.reject[it])
+        X = states[it]["F"].astype(np.float64)
+        assert np.allclose(X, ref.F[it], rtol=1e-7, atol=0), it      # X^2 stored as FP32
+    return rep
+
+
+def test_cppm_tiny_config_full_trajectory():
+    """The tiny configuration (step edge at x = 0.5) with the count test:
+    radii, windows, X^2 and estimate against the oracle, iteration by
+    iteration."""
+    sc = synth.PlaneScene(nside=64, J=100_000, r0=0.02, step=True)
+    iters = 16
+    hp = sc.hitpoints("cuda")
+    batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
+    states, stats, L = run_gpu(hp, batches, sc.r0, params=_params(test=1))
+    ref = O.run(hp.numpy(), synth.stack_numpy(batches), sc.r0, iters, test=1)
+    _cppm_check(states, stats, L, ref, iters)
+    assert 0 < ref.reject.sum() < ref.reject.size
+
+
+def test_cppm_box_scene_with_normals():
+    """Three faces of the unit box (same-surface test), lobes and shadows."""
+    sc = _box(seed=4)
+    iters = 8
+    hp = sc.hitpoints("cuda")
+    batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
+    states, stats, L = run_gpu(hp, batches, sc.r0, params=_params(test=1, cell_factor=0.6))
+    ref = O.run(hp.numpy(), synth.stack_numpy(batches), sc.r0, iters, test=1)
+    _cppm_check(states, stats, L, ref, iters)
+
+
+def test_cppm_box_scene_rgb_vcm():
+    """RGB flux with VCM+ weights: the counts decide, the weighted RGB
+    estimate follows the radii."""
+    sc = _box(rgb=True, vcm=True, seed=5)
+    iters = 5
+    hp = sc.hitpoints("cuda")
+    batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
+    p = _params(channels=3, vcm=1, k=0.9, test=1)
+    states, stats, L = run_gpu(hp, batches, sc.r0, params=p)
+    ref = O.run(hp.numpy(), synth.stack_numpy(batches), sc.r0, iters, k=0.9, vcm=True, test=1)
+    _cppm_check(states, stats, L, ref, iters)
+
+
+def test_cppm_argument_checks():
+    import torch
+    from paper_2504_04411_gb300 import ppm
+    sc = synth.PlaneScene(nside=8, J=1000, r0=0.1)
+    hp = sc.hitpoints("cuda")
+    for kw in ({"test": 2}, {"test": -1}, {"test": 1, "channels": 3, "rgb_test": 1}):
+        with pytest.raises(ppm.PPMError) as e:
+            ppm.Estimator(hp, sc.r0, 0.75, _params(**kw))
+        assert e.value.code == ppm.PPM_EINVAL
+    est = ppm.Estimator(hp, sc.r0, 0.75, _params(test=1))
+    with pytest.raises(ppm.PPMError) as e:
+        ppm.ppm_set_features(est.ctx, True)
+    assert e.value.code == ppm.PPM_EINVAL
+    est.close()
+    out = torch.empty(1, device="cuda", dtype=torch.float64)
+    for dof, a in ((0, 0.01), (1001, 0.01), (11, 0.0), (11, 1.0)):
+        with pytest.raises(ppm.PPMError):
+            ppm.ppm_chi2_critical(dof, a, out)
+
+
 # --------------------------------------------------------- plane scenes ----
 MAPPINGS = [0, 1, 2, 3, 4]
 
