@@ -179,7 +179,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="frame", choices=["frame", "tiny", "batched", "learned", "vcm", "cppm"])
+    ap.add_argument("--config", default="frame",
+                    choices=["frame", "tiny", "batched", "learned", "vcm", "cppm", "sweep"])
     ap.add_argument("--mapping", type=int, default=None, help="skip the autotuner: traversal")
     ap.add_argument("--cell-factor", type=float, default=None, help="skip the autotuner: cell factor")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -187,7 +188,8 @@ def parse():
     ap.add_argument("--no-flush", action="store_true")
     a = ap.parse_args()
     if a.steps is None:
-        a.steps = 16 if a.config in ("batched", "vcm") else (64 if a.config in ("learned", "cppm") else 64 - a.warmup)
+        a.steps = 16 if a.config in ("batched", "vcm") else (64 if a.config in ("learned", "cppm", "sweep")
+                                                             else 64 - a.warmup)
     return a
 
 
@@ -261,6 +263,8 @@ def main():
         line = run_learned(args, rank, world, local, dist)
     elif args.config == "cppm":
         line = run_cppm(args, rank, world, local, dist)
+    elif args.config == "sweep":
+        line = run_sweep(args, rank, world, local, dist)
     else:
         line = run_single(args, rank, world, local, dist)
     if rank == 0:
@@ -572,6 +576,43 @@ def run_learned(args, rank, world, local, dist):
                          "seconds": train_s}}
 
 
+def _mse_run(sc, hp, ref, N, r0, params):
+    """N iterations of one context on the scene's photons: per-iteration
+    device ms (grid build + gather), MSE of the running estimate against
+    ref, pairs, rejections and the final mean radius over r0."""
+    import torch
+
+    from paper_2504_04411_gb300 import ppm
+    stream = torch.cuda.current_stream()
+    est = ppm.Estimator(hp, r0, 0.75, params)
+    ms, mse, pairs, rejects = [], [], 0, 0
+    for i in range(1, N + 1):
+        ph = sc.photons(i, "cuda")
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        est.step(ph)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+        mse.append(float(((est.radiance() - ref) ** 2).mean()))
+        s = est.stats()
+        pairs += s.pairs
+        rejects += s.rejects
+    r = est.state()["r"]
+    est.close()
+    return ms, mse, pairs, rejects, float(r.mean()) / r0
+
+
+def _params(args, **kw):
+    from paper_2504_04411_gb300 import ppm
+    p = ppm.ppm_default_params()
+    p.mapping = args.mapping if args.mapping is not None else 0
+    p.cell_factor = args.cell_factor if args.cell_factor is not None else 0.6
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
 def run_cppm(args, rank, world, local, dist):
     """The paper's F-test (FPPM) against CPPM's chi-square test of the
     counts (Sec. 3.2.3, compared in Sec. 6.1.1) on the frame-sized scene,
@@ -581,38 +622,13 @@ def run_cppm(args, rank, world, local, dist):
     pair-test rate (device time of grid build + gather per iteration)."""
     import torch
 
-    from paper_2504_04411_gb300 import learned, ppm
+    from paper_2504_04411_gb300 import learned
     N = args.steps if args.steps else 64
     sc, desc = make_scene("frame", rank)
     hp = sc.hitpoints("cuda")
     ref = sc.irradiance(hp).to("cuda", torch.float32)
-    stream = torch.cuda.current_stream()
-
-    def timed(test):
-        p = ppm.ppm_default_params()
-        p.test = test
-        p.mapping = args.mapping if args.mapping is not None else 0
-        p.cell_factor = args.cell_factor if args.cell_factor is not None else 0.6
-        est = ppm.Estimator(hp, sc.r0, 0.75, p)
-        ms, mse, pairs, rejects = [], [], 0, 0
-        for i in range(1, N + 1):
-            ph = sc.photons(i, "cuda")
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            est.step(ph)
-            b.record(stream)
-            b.synchronize()
-            ms.append(a.elapsed_time(b))
-            mse.append(float(((est.radiance() - ref) ** 2).mean()))
-            s = est.stats()
-            pairs += s.pairs
-            rejects += s.rejects
-        r = est.state()["r"]
-        est.close()
-        return ms, mse, pairs, rejects, float(r.mean()) / sc.r0
-
-    fms, fmse, fpairs, frej, fr = timed(0)
-    cms, cmse, cpairs, crej, cr = timed(1)
+    fms, fmse, fpairs, frej, fr = _mse_run(sc, hp, ref, N, sc.r0, _params(args, test=0))
+    cms, cmse, cpairs, crej, cr = _mse_run(sc, hp, ref, N, sc.r0, _params(args, test=1))
     c_reach = learned.iterations_to_reach(cmse, fmse[-1])
     f_reach = learned.iterations_to_reach(fmse, cmse[-1])
     at = {k: {"fppm": fmse[k - 1], "cppm": cmse[k - 1]} for k in (8, 16, 32, 64) if k <= N}
@@ -628,6 +644,41 @@ def run_cppm(args, rank, world, local, dist):
                              "mean_final_radius_over_r0": {"fppm": fr, "cppm": cr},
                              "ms_per_iteration": {"fppm": sum(fms) / N, "cppm": sum(cms) / N},
                              "pairs_per_s": {"fppm": fpairs / (sum(fms) / 1e3), "cppm": cpairs / (sum(cms) / 1e3)}}}
+
+
+SWEEP = {"k": (0.5, 0.6, 0.7, 0.8, 0.9), "alpha_f": (0.001, 0.01, 0.05, 0.1), "r0": (0.005, 0.01, 0.02, 0.04)}
+
+
+def run_sweep(args, rank, world, local, dist):
+    """One parameter at a time around the paper's settings (k = 0.7,
+    alpha_F = 0.01, r0 = 0.01 here): the shrink ratio k (the analogue of
+    Table tab:k), the significance level alpha_F (Table tab:alpha) and the
+    initial radius r0 (Fig. fig:initial-bandwidth), each run for the same
+    iterations on the frame-sized scene's photons, MSE against the closed-
+    form irradiance.  The metric is the default setting's pair-test rate."""
+    import torch
+    N = args.steps if args.steps else 64
+    sc, desc = make_scene("frame", rank)
+    hp = sc.hitpoints("cuda")
+    ref = sc.irradiance(hp).to("cuda", torch.float32)
+    out, base = {}, None
+    for name, values in SWEEP.items():
+        out[name] = {}
+        for v in values:
+            r0 = v if name == "r0" else sc.r0
+            kw = {name: v} if name in ("k", "alpha_f") else {}
+            ms, mse, pairs, rej, rr = _mse_run(sc, hp, ref, N, r0, _params(args, **kw))
+            out[name][str(v)] = {"mse_at_16": mse[15] if N >= 16 else None, "mse_final": mse[-1],
+                                 "ms_per_iteration": sum(ms) / N, "rejects": rej,
+                                 "mean_final_radius_over_r0": rr}
+            if name == "k" and v == 0.7:
+                base = (pairs, sum(ms))
+    return {"metric": METRIC, "value": base[0] / (base[1] / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": N, "warmup": 0, "ms_per_step": base[1] / N, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(desc, workload="parameter sweep: " + desc["workload"], l2="not flushed",
+                           parallelism="single GPU", mapping=0, cell_factor=0.6, iterations=N),
+            "sweep": out}
 
 
 def run_reference(args):
