@@ -45,7 +45,8 @@ class _Params(ctypes.Structure):
                 ("r_min", ctypes.c_float), ("n_vm", ctypes.c_float),
                 ("alpha_f", ctypes.c_double), ("rgb_test", ctypes.c_int32),
                 ("vcm", ctypes.c_int32), ("i0", ctypes.c_int32),
-                ("test", ctypes.c_int32)]
+                ("test", ctypes.c_int32), ("retrace", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
 
 _lib = None
@@ -181,7 +182,7 @@ class OracleResult:
 
 def run(hp: dict, photons: dict, r_init, iters: int, *, k=0.7, alpha=0.75,
         r_min=None, alpha_f=0.01, rgb_test=False, vcm=False, n_vm=None,
-        i0=1, test=0, outputs=True) -> OracleResult:
+        i0=1, test=0, hp_iters=None, outputs=True) -> OracleResult:
     """Run the method for ``iters`` iterations over brute-force all pairs.
 
     hp: dict with pos (nh,3), u (nh,3), v (nh,3) float32 and optional
@@ -191,7 +192,16 @@ def run(hp: dict, photons: dict, r_init, iters: int, *, k=0.7, alpha=0.75,
         rho (iters,J,2) float32 and wq (iters,J) uint32.
     test: 0 for the ANOVA F-test, 1 for CPPM's chi-square test of the
         counts (then F holds X^2 and Fc holds chi_c).
+    hp_iters: optional list of ``iters`` hit-point dicts like hp, the hit
+        points traced anew for each iteration (same count and order: entry
+        h is the same pixel, whose statistics carry over); hp then only
+        gives the count.
     """
+    if hp_iters is not None:
+        if len(hp_iters) < iters:
+            raise ValueError("hp_iters needs one hit-point set per iteration")
+        hp = {k: np.concatenate([np.asarray(d[k]) for d in hp_iters[:iters]])
+              for k in hp_iters[0] if hp_iters[0][k] is not None}
     pos = np.ascontiguousarray(hp["pos"], np.float32)
     nh = pos.shape[0]
     hu = np.ascontiguousarray(hp["u"], np.float32)
@@ -200,6 +210,8 @@ def run(hp: dict, photons: dict, r_init, iters: int, *, k=0.7, alpha=0.75,
     hnq = None if hnq is None else np.ascontiguousarray(hnq, np.uint32)
     hrho = hp.get("rho")
     hrho = None if hrho is None else np.ascontiguousarray(hrho, np.float32)
+    if hp_iters is not None:
+        nh //= iters
     r_init = np.ascontiguousarray(np.broadcast_to(np.float32(r_init) if np.isscalar(r_init) else r_init, (nh,)), np.float32)
     ppos = np.ascontiguousarray(photons["pos"][:iters], np.float32)
     J = ppos.shape[1]
@@ -215,7 +227,8 @@ def run(hp: dict, photons: dict, r_init, iters: int, *, k=0.7, alpha=0.75,
         r_min = 1e-3 * float(np.max(r_init)) if nh else 0.0
     prm = _Params(k=k, alpha=alpha, r_min=r_min,
                   n_vm=float(J if n_vm is None else n_vm), alpha_f=alpha_f,
-                  rgb_test=int(rgb_test), vcm=int(vcm), i0=i0, test=int(test))
+                  rgb_test=int(rgb_test), vcm=int(vcm), i0=i0, test=int(test),
+                  retrace=int(hp_iters is not None), pad=0)
     if outputs:
         o_r = np.zeros((iters + 1, nh), np.float32)
         o_c = np.zeros((iters, nh, NG), np.int32)

@@ -344,6 +344,10 @@ typedef struct {
     int32_t i0;       /* global index of the first iteration (1-based) */
     int32_t test;     /* 0: ANOVA F-test (FPPM); 1: chi-square test of the
                          window's counts (CPPM, Sec. 3.2.3) decides alone */
+    int32_t retrace;  /* 1: the hit-point arrays hold one set per iteration
+                         (eye paths traced anew each iteration, the pixel's
+                         statistics carried over, as in SPPM) */
+    int32_t pad;
 } oracle_params;
 
 typedef struct {
@@ -400,6 +404,8 @@ static double or_window_f(const or_window* w, int nch, int ch, double m,
  * Inputs (all host arrays, row-major):
  *   hp_pos, hp_u, hp_v: nh*3 float; hp_nq: nh packed snorm8 normals or NULL;
  *   hp_rho: nh*2 float (rho_vm_h, rho_vc_h) for VCM+, else NULL;
+ *   with prm->retrace every hit-point array holds iters consecutive sets
+ *   (iters*nh entries), the set of iteration it used in iteration it;
  *   r_init: nh float initial radii (windows start empty, t = 0);
  *   ph_pos: iters*J*3 float; ph_flux: iters*J*nch float (nch = 1 or 3);
  *   ph_nq: iters*J packed normals or NULL; ph_rho: iters*J*2 float
@@ -452,11 +458,18 @@ int oracle_run(int64_t nh, const float* hp_pos, const float* hp_u,
         const float* xh = hp_pos + 3 * h;
         const float* u = hp_u + 3 * h;
         const float* v = hp_v + 3 * h;
+        int64_t hi = h;           /* this iteration's entry of hit point h */
         float r = r_init[h];
         int32_t t = 0;
         double tau[3] = {0.0, 0.0, 0.0};
         or_window win = {0, 0, NULL, NULL};
         for (int it = 0; it < iters; ++it) {
+            if (prm->retrace) {
+                hi = (int64_t)it * nh + h;
+                xh = hp_pos + 3 * hi;
+                u = hp_u + 3 * hi;
+                v = hp_v + 3 * hi;
+            }
             const float* P = ph_pos + (size_t)it * J * 3;
             const float* PHI = ph_flux + (size_t)it * J * nch;
             if (out_r) out_r[(size_t)it * nh + h] = r;
@@ -465,14 +478,14 @@ int oracle_run(int64_t nh, const float* hp_pos, const float* hp_u,
             for (int64_t p = 0; p < J; ++p) {
                 size_t gp = (size_t)it * J + p;
                 int g = oracle_classify(xh, u, v, r, P + 3 * p, use_normals,
-                                        use_normals ? hp_nq[h] : 0,
+                                        use_normals ? hp_nq[hi] : 0,
                                         use_normals ? ph_nq[gp] : 0);
                 if (g < 0) continue;
                 pairs++;
                 double w = 1.0;
                 if (prm->vcm) {
-                    int cd = oracle_normal_dot(hp_nq[h], ph_wq[gp]);
-                    w = oracle_mis_weight(hp_rho[2 * h], hp_rho[2 * h + 1],
+                    int cd = oracle_normal_dot(hp_nq[hi], ph_wq[gp]);
+                    w = oracle_mis_weight(hp_rho[2 * hi], hp_rho[2 * hi + 1],
                                           ph_rho[2 * gp], ph_rho[2 * gp + 1],
                                           cd, prm->n_vm, (double)r);
                 }

@@ -119,6 +119,22 @@ class PlaneScene:
         v = torch.tensor([0.0, 1.0, 0.0]).expand(n * n, 3).contiguous()
         return HitPoints(pos.to(device), u.to(device), v.to(device), None, None)
 
+    def hitpoints_jittered(self, it: int, device="cpu") -> HitPoints:
+        """The hit points of iteration it traced anew through a random point
+        of each pixel (SPPM-style stochastic eye paths): pixel (i, j) lands at
+        ((i + a) / n, (j + b) / n, 0) with a, b uniform in [0, 1).  Same count
+        and order as hitpoints(): entry h is always the same pixel."""
+        n = self.nside
+        g = _gen(self.seed, 100_000 + it, "cpu")
+        ab = torch.rand(n * n, 2, generator=g, dtype=torch.float64)
+        c = torch.arange(n, dtype=torch.float64)
+        yy, xx = torch.meshgrid(c, c, indexing="ij")
+        pos = torch.stack([(xx.flatten() + ab[:, 0]) / n, (yy.flatten() + ab[:, 1]) / n,
+                           torch.zeros(n * n, dtype=torch.float64)], 1).float()
+        u = torch.tensor([1.0, 0.0, 0.0]).expand(n * n, 3).contiguous()
+        v = torch.tensor([0.0, 1.0, 0.0]).expand(n * n, 3).contiguous()
+        return HitPoints(pos.to(device), u.to(device), v.to(device), None, None)
+
     def photons(self, it: int, device="cpu") -> Photons:
         g = _gen(self.seed, it, device)
         J = self.J

@@ -423,3 +423,55 @@ def test_step_edge_expected_estimate_closed_form():
     want = np.array([lit_fraction(float(d)) for d in offs])
     lam = 40000 * math.pi * r * r
     assert np.all(np.abs(est - want) < 5 / math.sqrt(lam * runs) + 1e-3)
+
+
+# ------------------------------------------ hit points traced anew ----------
+def test_retrace_with_the_same_hit_points_equals_the_static_run():
+    # one hit-point set per iteration, all equal: exactly the static method
+    sc = synth.PlaneScene(nside=24, J=10000, r0=0.05, step=True)
+    hp = sc.hitpoints().numpy()
+    iters = 6
+    ph = synth.stack_numpy([sc.photons(i) for i in range(1, iters + 1)])
+    a = O.run(hp, ph, sc.r0, iters)
+    b = O.run(hp, ph, sc.r0, iters, hp_iters=[hp] * iters)
+    for f in ("r", "counts", "S", "Q", "F", "reject", "pairs", "t", "tau"):
+        assert np.array_equal(getattr(a, f), getattr(b, f)), f
+
+
+def test_retrace_uses_each_iterations_hit_points():
+    # the pairs of iteration i are those of iteration i's positions (FP64
+    # geometry brackets them), and the statistics of a pixel carry over
+    sc = synth.PlaneScene(nside=16, J=5000, r0=0.06, step=True)
+    iters = 4
+    hps = [sc.hitpoints_jittered(i).numpy() for i in range(1, iters + 1)]
+    batches = [sc.photons(i) for i in range(1, iters + 1)]
+    ph = synth.stack_numpy(batches)
+    res = O.run(hps[0], ph, sc.r0, iters, hp_iters=hps)
+    for it in range(iters):
+        r = res.r[it].astype(np.float64)
+        d = hps[it]["pos"][:, None, :2].astype(np.float64) - ph["pos"][it][None, :, :2]
+        d2 = (d ** 2).sum(-1)
+        lo = (d2 <= (r[:, None] * (1 - 1e-6)) ** 2).sum(1)
+        hi = (d2 <= (r[:, None] * (1 + 1e-6)) ** 2).sum(1)
+        assert np.all(res.pairs[it] >= lo) and np.all(res.pairs[it] <= hi), it
+    for it in range(1, iters):
+        keep = ~res.reject[it - 1]
+        assert np.array_equal(res.counts[it][keep].sum(1), res.counts[it - 1][keep].sum(1) + res.pairs[it][keep])
+    # jitter moves the disks: a static run on the same photons differs
+    static = O.run(hps[0], ph, sc.r0, iters)
+    assert not np.array_equal(static.pairs[1:], res.pairs[1:])
+
+
+def test_retrace_constant_plane_unbiased():
+    # constant irradiance: each iteration's estimate is unbiased wherever its
+    # hit point lands, so the mean over pixels and iterations is the density
+    sc = synth.PlaneScene(nside=32, J=20000, r0=0.04, step=False, lo=-0.05, hi=1.05)
+    iters = 6
+    hps = [sc.hitpoints_jittered(i).numpy() for i in range(1, iters + 1)]
+    ph = synth.stack_numpy([sc.photons(i) for i in range(1, iters + 1)])
+    res = O.run(hps[0], ph, sc.r0, iters, hp_iters=hps)
+    L = res.tau[:, 0] / iters
+    E = sc.irradiance_density()
+    lam = sc.J * math.pi * sc.r0 ** 2 / (sc.hi - sc.lo) ** 2
+    se = E / math.sqrt(lam * iters * L.size)
+    assert abs(L.mean() - E) < 8 * se * math.sqrt(math.pi * (sc.r0 * 32) ** 2)
