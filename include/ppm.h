@@ -178,6 +178,18 @@ int ppm_create(const ppm_hitpoints* hp, float r0, float alpha,
 /* Change the stream later work is enqueued on. */
 int ppm_set_stream(ppm_ctx* ctx, void* stream);
 
+/* Hit points traced anew (stochastic eye paths through each pixel, as in
+ * SPPM, which the paper's distributed ray tracing stage follows, Sec. 7):
+ * replace the positions, frames, normals and VCM+ ratios of all n hit
+ * points before an iteration's ppm_build_grid / ppm_gather_test_update.
+ * hp has the same count and order as at ppm_create: entry h is the same
+ * pixel, whose radius, window statistics and estimate carry over.  The
+ * context keeps the spatial order it computed at ppm_create.  hp->nq must
+ * be given iff it was at create (the same-surface test stays on or off),
+ * hp->rho when the context is VCM+.  The arrays may be reused once the
+ * stream passes this work.  PPM_EINVAL on a count or array mismatch. */
+int ppm_set_hitpoints(ppm_ctx* ctx, const ppm_hitpoints* hp);
+
 /* Step 1 of an iteration (Sec. 5.1: build the range-search structure):
  * hash every photon to a grid cell of edge cell_factor * max_h r_h, sort
  * (cell, index) pairs with a stable radix sort, and copy the photons into

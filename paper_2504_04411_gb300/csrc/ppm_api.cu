@@ -111,7 +111,7 @@ __global__ void k_hp_permute(int64_t n, const uint32_t* __restrict__ vals,
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t j = vals[i];
-    orig[i] = (uint32_t)j;
+    if (orig) orig[i] = (uint32_t)j;   // NULL: the order is kept
     hp_pos[i] = make_float4(pos[3 * j], pos[3 * j + 1], pos[3 * j + 2],
                             __uint_as_float(nq ? nq[j] : 0u));
     hp_u[i] = make_float4(u[3 * j], u[3 * j + 1], u[3 * j + 2], rho ? rho[2 * j] : 0.f);
@@ -637,6 +637,24 @@ int ppm_f_critical(int64_t J, double alpha_f, int32_t t_max, double* out, void* 
     cudaStream_t st = (cudaStream_t)stream;
     PPM_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
     return ppm_fcrit_fill(out, 1, t_max, (double)J, alpha_f, st);
+}
+
+int ppm_set_hitpoints(ppm_ctx* c, const ppm_hitpoints* hp)
+{
+    PPM_ENTRY();
+    if (!c || !hp || hp->n != c->nh) return PPM_EINVAL;
+    if (c->nh == 0) return PPM_OK;
+    if (!hp->pos || !hp->u || !hp->v) return PPM_EINVAL;
+    if ((hp->nq != nullptr) != c->normals) return PPM_EINVAL;
+    if (c->prm.vcm && !hp->rho) return PPM_EINVAL;
+    // internal slot i holds caller entry hp_orig[i]: gather the new arrays
+    // into the same slots
+    const unsigned nb = (unsigned)((c->nh + 255) / 256);
+    k_hp_permute<<<nb, 256, 0, c->stream>>>(c->nh, c->hp_orig, hp->pos, hp->u, hp->v, hp->nq,
+                                           c->prm.vcm ? hp->rho : nullptr, nullptr, c->hp_pos, c->hp_u,
+                                           c->hp_v);
+    PPM_LAUNCH_CHECK();
+    return PPM_OK;
 }
 
 int ppm_chi2_critical(int32_t dof, double alpha, double* out, void* stream)

@@ -60,6 +60,7 @@ class ppm_state_view(ctypes.Structure):
 EXPORTS = ("ppm_default_params", "ppm_create", "ppm_set_stream", "ppm_build_grid",
            "ppm_gather_test_update", "ppm_radiance", "ppm_get_state", "ppm_set_state",
            "ppm_set_iteration", "ppm_stats", "ppm_f_critical", "ppm_chi2_critical", "ppm_sort_pairs",
+           "ppm_set_hitpoints",
            "ppm_destroy", "ppm_strerror", "ppm_sort_pairs_noalloc",
            "ppm_batch_create", "ppm_batch_iterate", "ppm_batch_radiance",
            "ppm_batch_get_state", "ppm_batch_stats", "ppm_batch_graph_ready",
@@ -85,6 +86,8 @@ def load(path: str = LIB_PATH):
                              ctypes.POINTER(ppm_params), c_p, ctypes.POINTER(c_p)]
     L.ppm_set_stream.restype = ctypes.c_int
     L.ppm_set_stream.argtypes = [c_p, c_p]
+    L.ppm_set_hitpoints.restype = ctypes.c_int
+    L.ppm_set_hitpoints.argtypes = [c_p, ctypes.POINTER(ppm_hitpoints)]
     L.ppm_build_grid.restype = ctypes.c_int
     L.ppm_build_grid.argtypes = [c_p, ctypes.POINTER(ppm_photons)]
     L.ppm_gather_test_update.restype = ctypes.c_int
@@ -207,6 +210,12 @@ def ppm_create(pos, u, v, r0: float, alpha: float = 0.75, params: ppm_params | N
 
 def ppm_set_stream(ctx, stream=None) -> None:
     _check("ppm_set_stream", load().ppm_set_stream(ctx, _stream(stream)))
+
+
+def ppm_set_hitpoints(ctx, pos, u, v, nq=None, rho=None) -> None:
+    """Hit points traced anew (same count and order as at ppm_create)."""
+    hp = ppm_hitpoints(pos.shape[0], _ptr(pos), _ptr(u), _ptr(v), _ptr(nq), _ptr(rho))
+    _check("ppm_set_hitpoints", load().ppm_set_hitpoints(ctx, ctypes.byref(hp)))
 
 
 def ppm_build_grid(ctx, pos, flux, J: int, nq=None, rho=None, wq=None) -> None:
@@ -347,6 +356,12 @@ class Estimator:
         self.ctx = ppm_create(hp.pos, hp.u, hp.v, r0, alpha, self.params,
                               nq=hp.nq, rho=hp.rho if self.params.vcm else None, stream=stream)
         self.it = 0
+
+    def retrace(self, hp) -> None:
+        """This iteration's hit points (SPPM-style): same pixels, new
+        positions; statistics carry over."""
+        ppm_set_hitpoints(self.ctx, hp.pos, hp.u, hp.v, nq=hp.nq,
+                          rho=hp.rho if self.params.vcm else None)
 
     def step(self, ph, J: int | None = None) -> None:
         ppm_build_grid(self.ctx, ph.pos, ph.flux, J if J is not None else ph.pos.shape[0],

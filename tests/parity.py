@@ -28,13 +28,16 @@ class Report:
     pairs_checked: int = 0
 
 
-def run_gpu(hp, batches, r0, alpha=0.75, params=None, J=None):
+def run_gpu(hp, batches, r0, alpha=0.75, params=None, J=None, hps=None):
+    """hps: optional hit points traced anew for every iteration."""
     import torch
 
     from paper_2504_04411_gb300 import ppm
     est = ppm.Estimator(hp, r0, alpha, params)
     states, stats = [], []
-    for ph in batches:
+    for i, ph in enumerate(batches):
+        if hps is not None:
+            est.retrace(hps[i])
         est.step(ph, J)
         st = est.state()
         states.append({k: v.cpu().numpy() for k, v in st.items()})

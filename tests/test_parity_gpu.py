@@ -137,6 +137,53 @@ def test_cppm_argument_checks():
             ppm.ppm_chi2_critical(dof, a, out)
 
 
+# ------------------------------------------ hit points traced anew ------
+@pytest.mark.parametrize("mapping", [0, 1, 4])
+def test_retraced_hit_points_full_trajectory(mapping):
+    """SPPM-style pixels: each iteration's hit points land at a new random
+    point of their pixel (ppm_set_hitpoints), statistics carried per pixel;
+    the whole trajectory against the oracle on the same positions."""
+    sc = synth.PlaneScene(nside=64, J=100_000, r0=0.02, step=True)
+    iters = 12
+    hps = [sc.hitpoints_jittered(i, "cuda") for i in range(1, iters + 1)]
+    batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
+    states, stats, L = run_gpu(hps[0], batches, sc.r0, params=_params(mapping=mapping), hps=hps)
+    ref = O.run(hps[0].numpy(), synth.stack_numpy(batches), sc.r0, iters,
+                hp_iters=[h.numpy() for h in hps])
+    rep = compare(states, stats, L, ref, iters)
+    assert rep.diverged <= 4, rep
+    assert ref.reject.sum() > 50
+
+
+def test_retrace_with_the_same_hit_points_is_bit_identical():
+    sc = synth.PlaneScene(nside=40, J=50_000, r0=0.03, step=True)
+    iters = 6
+    hp = sc.hitpoints("cuda")
+    batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
+    a = run_gpu(hp, batches, sc.r0)
+    b = run_gpu(hp, batches, sc.r0, hps=[sc.hitpoints("cuda") for _ in range(iters)])
+    for sa, sb in zip(a[0], b[0]):
+        for k in sa:
+            assert np.array_equal(sa[k], sb[k]), k
+    assert np.array_equal(a[2], b[2])
+
+
+def test_set_hitpoints_argument_checks():
+    import torch
+    from paper_2504_04411_gb300 import ppm
+    sc = synth.PlaneScene(nside=8, J=1000, r0=0.1)
+    hp = sc.hitpoints("cuda")
+    est = ppm.Estimator(hp, sc.r0, 0.75)
+    small = synth.PlaneScene(nside=7).hitpoints("cuda")
+    nq = torch.zeros(hp.n, dtype=torch.int32, device="cuda")
+    for args, kw in (((small.pos, small.u, small.v), {}),            # another count
+                     ((hp.pos, hp.u, hp.v), {"nq": nq})):           # normals the context lacks
+        with pytest.raises(ppm.PPMError) as e:
+            ppm.ppm_set_hitpoints(est.ctx, *args, **kw)
+        assert e.value.code == ppm.PPM_EINVAL
+    est.close()
+
+
 # --------------------------------------------------------- plane scenes ----
 MAPPINGS = [0, 1, 2, 3, 4]
 
