@@ -37,6 +37,7 @@ def test_default_params_and_strerror_without_gpu():
     p = ppm.ppm_default_params()
     assert p.k == pytest.approx(0.7) and p.alpha_f == pytest.approx(0.01)
     assert p.rmin_ratio == pytest.approx(1e-3) and p.cell_factor == 1.0
+    assert p.test == 0 and p.mapping == 0 and p.tile == 0 and list(p.reserved) == [0] * 4
     assert ppm.ppm_strerror(ppm.PPM_ESTATE) == "call out of order"
 
 
@@ -48,3 +49,35 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(ppm.ppm_params) == 64
     assert ctypes.sizeof(ppm.ppm_iter_stats) == 64
     assert ctypes.sizeof(ppm.ppm_state_view) == 56
+
+
+def test_struct_field_offsets_match_the_header(tmp_path):
+    """Every field of the binding's structs at the offset the C compiler
+    gives it in include/ppm.h (a renamed, moved or resized field fails)."""
+    import shutil
+    import subprocess
+
+    from paper_2504_04411_gb300 import ppm
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    names = ("ppm_hitpoints", "ppm_photons", "ppm_params", "ppm_iter_stats", "ppm_state_view")
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "ppm.h"', "int main(void)", "{"]
+    for s in names:
+        lines.append(f'    printf("{s} %zu\\n", sizeof({s}));')
+        for f, _ in getattr(ppm, s)._fields_:
+            lines.append(f'    printf("{s}.{f} %zu\\n", offsetof({s}, {f}));')
+    lines += ["    return 0;", "}"]
+    src, exe = tmp_path / "offsets.c", tmp_path / "offsets"
+    src.write_text("\n".join(lines) + "\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([cc, "-std=c11", "-Wall", "-Werror", str(src), "-o", str(exe),
+                        "-I", os.path.join(root, "include")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    for s in names:
+        cls = getattr(ppm, s)
+        assert int(got[s]) == ctypes.sizeof(cls), s
+        for f, _ in cls._fields_:
+            assert int(got[f"{s}.{f}"]) == getattr(cls, f).offset, f"{s}.{f}"
