@@ -50,6 +50,9 @@ extern "C" {
 #define PPM_ECUDA    (-3)   /* a CUDA runtime call or launch failed */
 #define PPM_ETIMEOUT (-4)   /* a bounded device-side wait gave up */
 #define PPM_ESTATE   (-5)   /* call out of order (iteration sequence) */
+#define PPM_EINCOMPLETE (-6) /* a gather skipped cells: a hit point's sphere
+                               spanned more grid cells than a hash block, so
+                               some of its photons were not gathered */
 
 #define PPM_NGROUPS 12      /* 2 annuli x 6 sectors, Sec. 6.1.1 */
 
@@ -123,18 +126,28 @@ typedef struct {
                            array of ppm_get_state then holds.  Contexts only
                            (batches: PPM_EINVAL); not with rgb_test, features
                            or the proposer (PPM_EINVAL); traversal 0. */
-    int32_t reserved[4];
+    int32_t wait_limit; /* polls before a wait between the blocks of the grid's
+                           sort gives up (decoupled look-back); 0 = the default
+                           (2^22, each poll sleeping ~32 ns).  The waits always
+                           end on a healthy GPU; a small limit only exists to
+                           test the error path (PPM_ETIMEOUT below). */
+    int32_t reserved[3];
 } ppm_params;
 
 /* Per-iteration counters of the last ppm_gather_test_update. */
 typedef struct {
     int32_t iter;          /* last completed iteration (0 = none) */
-    int32_t flags;         /* device error flags; bit 0: a sphere spanned more
-                              cells than a hash block (results incomplete);
-                              bit 1: a window length outside the F_c table
-                              (from ppm_set_state), clamped; bit 2: a wait
-                              between the blocks of the grid's sort gave up
-                              (never expected; results unspecified) */
+    int32_t flags;         /* device error flags, sticky for the life of the
+                              context; bit 0: a sphere spanned more cells
+                              than a hash block (results incomplete; the
+                              counters' call returns PPM_EINCOMPLETE); bit 1:
+                              a window length outside the F_c table (from
+                              ppm_set_state), clamped; bit 2: a wait between
+                              the blocks of the grid's sort gave up (the
+                              grid is unusable: the cell ranges, the permute
+                              and every later gather of the context do
+                              nothing, and the counters' call returns
+                              PPM_ETIMEOUT) */
     int64_t pairs;         /* in-disk photon/hit-point pairs gathered */
     int64_t candidates;    /* photons visited in the scanned cells */
     int64_t rejects;       /* hit points whose null hypothesis was rejected */
@@ -209,12 +222,18 @@ int ppm_radiance(ppm_ctx* ctx, float* out);
 
 /* Copy the state out of / into the context (checkpoint / resume, tests).
  * Both wait for the copies to finish.  set_state leaves the iteration
- * counter untouched; use ppm_set_iteration to resume a sequence. */
+ * counter untouched; use ppm_set_iteration to resume a sequence.
+ * get_state copies the state and then returns PPM_ETIMEOUT or
+ * PPM_EINCOMPLETE when the context's error flags hold bit 2 or bit 0 (see
+ * ppm_iter_stats.flags). */
 int ppm_get_state(ppm_ctx* ctx, const ppm_state_view* v);
 int ppm_set_state(ppm_ctx* ctx, const ppm_state_view* v);
 int ppm_set_iteration(ppm_ctx* ctx, int32_t iter);
 
-/* Counters of the last iteration; waits for the stream. */
+/* Counters of the last iteration; waits for the stream.  *out is filled in
+ * every case; the return value is PPM_ETIMEOUT if a bounded device wait of
+ * the context has given up (flags bit 2), else PPM_EINCOMPLETE if a gather
+ * skipped cells (flags bit 0), else PPM_OK. */
 int ppm_stats(ppm_ctx* ctx, ppm_iter_stats* out);
 
 /* One whole iteration fed from HOST memory: the grid build of
@@ -233,7 +252,8 @@ int ppm_iterate_host(ppm_ctx* ctx, const ppm_photons* host_ph, int32_t iter);
 
 /* Counters of host-fed iteration iter, which must be one of the last two
  * ppm_iterate_host iterations (PPM_ESTATE otherwise): waits only for that
- * iteration's counter copy, not for later work.  gather_ms is -1. */
+ * iteration's counter copy, not for later work.  gather_ms is -1.  Returns
+ * PPM_ETIMEOUT / PPM_EINCOMPLETE from the flags as ppm_stats does. */
 int ppm_stats_host(ppm_ctx* ctx, int32_t iter, ppm_iter_stats* out);
 
 /* F-test critical values on their own (Sec. 3.2.2): out[t] = the
@@ -347,10 +367,11 @@ int ppm_batch_iterate(ppm_batch* b, const ppm_photons* ph, int32_t iter);
 /* Radiance of one problem into out (device, that problem's n or n x 3). */
 int ppm_batch_radiance(ppm_batch* b, int32_t problem, float* out);
 
-/* State of one problem (as ppm_get_state); waits. */
+/* State of one problem (as ppm_get_state, error returns included); waits. */
 int ppm_batch_get_state(ppm_batch* b, int32_t problem, const ppm_state_view* v);
 
-/* Counters of the last iteration, one entry per problem; waits. */
+/* Counters of the last iteration, one entry per problem; waits.  Returns
+ * PPM_ETIMEOUT / PPM_EINCOMPLETE from the batch's flags as ppm_stats does. */
 int ppm_batch_stats(ppm_batch* b, ppm_iter_stats* out);
 
 /* 1 once the iteration has been captured into a CUDA graph, else 0. */
@@ -366,18 +387,19 @@ const char* ppm_strerror(int code);
 /* ---- no-allocation variant (the paper has no counterpart) ----------------
  * ppm_sort_pairs_noalloc: the same stable radix sort as ppm_sort_pairs, with
  * the same arguments, results and error codes (computed by three kernels a
- * pass, with no waits between blocks), for callers that must not
- * allocate device memory while they run -- work recorded into a CUDA graph
- * (stream capture forbids cudaMalloc), real-time loops that cannot pay for
- * an allocator call or its implicit synchronization, hosts whose device
- * memory belongs to another allocator.  It calls no cudaMalloc, cudaFree or
- * other allocating routine: its scratch is a fixed device array of the
- * library, sized for PPM_NOALLOC_MAX_PAIRS pairs (~8.6 MB), which every GPU
- * that loads the library holds until the process exits.
+ * pass, with no waits between blocks), for callers that cannot call
+ * cudaMalloc while they run -- real-time loops that cannot pay for an
+ * allocator call or the synchronization it may bring, hosts whose device
+ * memory belongs to another allocator.  It calls no cudaMalloc, cudaFree
+ * or other allocating routine: its scratch is a fixed device array of the
+ * library, sized for PPM_NOALLOC_MAX_PAIRS = n pairs (2n + n/8 + 34 words,
+ * 8.9 MB), which every GPU that loads the library holds until the process
+ * exits.
  *   - n > PPM_NOALLOC_MAX_PAIRS returns PPM_EINVAL (use ppm_sort_pairs).
  *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress) with that device current and keeps it for the
+ *     life of the process: cudaDeviceReset after that first call is not
+ *     supported.
  *   - All calls share the array: calls whose work overlaps on the GPU
  *     (several streams or host threads on one device) race on it; order
  *     them on one stream.  It keeps the last call's contents; nothing in it

@@ -80,13 +80,15 @@ def lib():
         _lib.oracle_radius_bound.argtypes = [f, f, i]
         _lib.oracle_shrink.restype = f
         _lib.oracle_shrink.argtypes = [f, f, f]
+        _lib.oracle_lum.restype = d
+        _lib.oracle_lum.argtypes = [d, d, d]
         _lib.oracle_mis_weight.restype = d
         _lib.oracle_mis_weight.argtypes = [d, d, d, d, i, d, d]
         _lib.oracle_run.restype = i
         _lib.oracle_run.argtypes = [ctypes.c_int64, P, P, P, P, P, P, i,
                                     ctypes.c_int64, P, P, i, P, P, P,
                                     ctypes.POINTER(_Params),
-                                    P, P, P, P, P, P, P, P, P, P]
+                                    P, P, P, P, P, P, P, P, P, P, P]
     return _lib
 
 
@@ -160,6 +162,12 @@ def shrink(r: float, k: float, bound: float) -> float:
     return lib().oracle_shrink(r, k, bound)
 
 
+# -- Sec. 5.1: the tested luminance of an RGB flux -----------------------------
+def lum(R: float, G: float, B: float) -> float:
+    """Rec. 709 luminance (the paper tests luminance without naming weights)."""
+    return lib().oracle_lum(R, G, B)
+
+
 # -- Eq. (mis-weight) ---------------------------------------------------------
 def mis_weight(rho_vm_h, rho_vc_h, rho_vm_l, rho_vc_l, cos_dot, n_vm, r):
     return lib().oracle_mis_weight(rho_vm_h, rho_vc_h, rho_vm_l, rho_vc_l,
@@ -170,14 +178,17 @@ def mis_weight(rho_vm_h, rho_vc_h, rho_vm_l, rho_vc_l, cos_dot, n_vm, r):
 class OracleResult:
     r: np.ndarray          # (iters+1, nh) radius used per iteration, then final
     counts: np.ndarray     # (iters, nh, 12) window counts used by the test
-    S: np.ndarray          # (iters, nh, 12) window sums of psi
-    Q: np.ndarray          # (iters, nh, 12) window sums of psi^2
+    S: np.ndarray          # (iters, nh, 12) window sums of psi (tested channel 0)
+    Q: np.ndarray          # (iters, nh, 12) window sums of psi^2 (tested channel 0)
     F: np.ndarray          # (iters, nh)
     Fc: np.ndarray         # (iters, nh)
     reject: np.ndarray     # (iters, nh) bool
     pairs: np.ndarray      # (iters, nh) in-disk pairs of the iteration
     t: np.ndarray          # (nh,) final window length
     tau: np.ndarray        # (nh, nch) accumulated estimate sum
+    Sc: np.ndarray = None  # (iters, nh, ntest, 12) window sums of psi, every tested channel
+    Qc: np.ndarray = None  # (iters, nh, ntest, 12) window sums of psi^2, every tested channel
+    est: np.ndarray = None  # (iters, nh, nch) each iteration's term added to tau
 
 
 def run(hp: dict, photons: dict, r_init, iters: int, *, k=0.7, alpha=0.75,
@@ -229,17 +240,19 @@ def run(hp: dict, photons: dict, r_init, iters: int, *, k=0.7, alpha=0.75,
                   n_vm=float(J if n_vm is None else n_vm), alpha_f=alpha_f,
                   rgb_test=int(rgb_test), vcm=int(vcm), i0=i0, test=int(test),
                   retrace=int(hp_iters is not None), pad=0)
+    ntest = 3 if (rgb_test and nch == 3) else 1
     if outputs:
         o_r = np.zeros((iters + 1, nh), np.float32)
         o_c = np.zeros((iters, nh, NG), np.int32)
-        o_S = np.zeros((iters, nh, NG), np.float64)
-        o_Q = np.zeros((iters, nh, NG), np.float64)
+        o_S = np.zeros((iters, nh, ntest, NG), np.float64)
+        o_Q = np.zeros((iters, nh, ntest, NG), np.float64)
         o_F = np.zeros((iters, nh), np.float64)
         o_Fc = np.zeros((iters, nh), np.float64)
         o_rej = np.zeros((iters, nh), np.uint8)
         o_pairs = np.zeros((iters, nh), np.int32)
+        o_est = np.zeros((iters, nh, nch), np.float64)
     else:
-        o_r = o_c = o_S = o_Q = o_F = o_Fc = o_rej = o_pairs = None
+        o_r = o_c = o_S = o_Q = o_F = o_Fc = o_rej = o_pairs = o_est = None
     o_t = np.zeros(nh, np.int32)
     o_tau = np.zeros((nh, nch), np.float64)
     rc = lib().oracle_run(nh, _ptr(pos), _ptr(hu), _ptr(hv), _ptr(hnq),
@@ -247,12 +260,13 @@ def run(hp: dict, photons: dict, r_init, iters: int, *, k=0.7, alpha=0.75,
                           _ptr(flux), nch, _ptr(pnq), _ptr(prho), _ptr(pwq),
                           ctypes.byref(prm), _ptr(o_r), _ptr(o_c), _ptr(o_S),
                           _ptr(o_Q), _ptr(o_F), _ptr(o_Fc), _ptr(o_rej),
-                          _ptr(o_pairs), _ptr(o_t), _ptr(o_tau))
+                          _ptr(o_pairs), _ptr(o_t), _ptr(o_tau), _ptr(o_est))
     if rc != 0:
         raise ValueError(f"oracle_run rejected its arguments (rc={rc})")
-    return OracleResult(o_r, o_c, o_S, o_Q, o_F, o_Fc,
+    return OracleResult(o_r, o_c, None if o_S is None else o_S[:, :, 0, :],
+                        None if o_Q is None else o_Q[:, :, 0, :], o_F, o_Fc,
                         None if o_rej is None else o_rej.astype(bool),
-                        o_pairs, o_t, o_tau)
+                        o_pairs, o_t, o_tau, Sc=o_S, Qc=o_Q, est=o_est)
 
 
 if __name__ == "__main__":  # pragma: no cover

@@ -45,16 +45,20 @@
  *    quantile of F(d1, d2) with d1 = n-1 and d2 = n(m-1).
  *
  *    CDF_F(f; d1, d2) = I_x(d1/2, d2/2), x = d1 f / (d1 f + d2), where I is
- *    the regularized incomplete beta function.  I_x(a,b) is evaluated from
- *    its continued fraction (Lentz's method).  Of the two sides of the
- *    symmetry I_x(a,b) = 1 - I_{1-x}(b,a) the fraction is evaluated on the
- *    one where it converges fast (x < (a+1)/(a+b+2)), except when b >> a:
- *    there the other side's odd terms are -1 + O(1/b) and every step cancels
- *    ~9 digits, while the direct side stays well conditioned and converges
- *    in a few dozen terms.  The log-Beta prefactor is taken in quadruple
- *    precision (binary128: long double on aarch64, __float128 on x86-64)
- *    because lgamma(b) and lgamma(a+b) are ~1e11 at the sample sizes of
- *    this method.  The quantile is found by plain bisection on the CDF.
+ *    the regularized incomplete beta function.  I is evaluated from its
+ *    hypergeometric series (DLMF Sec. 8.17(ii)):
+ *        I_x(a,b) = x^a (1-x)^b / (a B(a,b)) * 2F1(a+b, 1; a+1; x)
+ *                 = x^a (1-x)^b / (a B(a,b)) * sum_{j>=0} (a+b)_j / (a+1)_j x^j,
+ *    ((q)_j the rising factorial), whose terms are all positive: no
+ *    cancellation.  The sum is taken on the side of the symmetry
+ *    I_x(a,b) = 1 - I_{1-x}(b,a) where its terms fall off fastest: the
+ *    direct side below x = (a+1)/(a+b+2), and always when b >> a (there x is
+ *    tiny, the direct terms behave like (b x)^j / j!, and the other side's
+ *    ratio tends to 1 - x ~ 1).  The series and the log-Beta prefactor are
+ *    taken in quadruple precision (binary128: long double on aarch64,
+ *    __float128 on x86-64) because lgamma(b) and lgamma(a+b) are ~1e11 at
+ *    the sample sizes of this method.  The quantile is found by plain
+ *    bisection on the CDF.
  * ---------------------------------------------------------------------- */
 #if defined(__x86_64__)
 #include <quadmath.h>
@@ -71,45 +75,28 @@ typedef long double or_quad;
 #define OR_EXP expl
 #endif
 
-static double or_beta_cf(double a, double b, double x)
+/* I_x(a,b) by the series above, on the side the caller chose (0 < x < 1) */
+static double or_beta_series(double a, double b, double x)
 {
-    const double tiny = 1e-300;
-    double c = 1.0, d = 1.0 - (a + b) * x / (a + 1.0), h;
-    if (fabs(d) < tiny) d = tiny;
-    d = 1.0 / d;
-    h = d;
-    for (int k = 1; k < 100000; ++k) {
-        double num, delta;
-        /* even step: d_{2k} = k (b-k) x / ((a+2k-1)(a+2k)) */
-        num = k * (b - k) * x / ((a + 2.0 * k - 1.0) * (a + 2.0 * k));
-        d = 1.0 + num * d; if (fabs(d) < tiny) d = tiny;
-        c = 1.0 + num / c; if (fabs(c) < tiny) c = tiny;
-        d = 1.0 / d;
-        h *= d * c;
-        /* odd step: d_{2k+1} = -(a+k)(a+b+k) x / ((a+2k)(a+2k+1)) */
-        num = -(a + k) * (a + b + k) * x / ((a + 2.0 * k) * (a + 2.0 * k + 1.0));
-        d = 1.0 + num * d; if (fabs(d) < tiny) d = tiny;
-        c = 1.0 + num / c; if (fabs(c) < tiny) c = tiny;
-        d = 1.0 / d;
-        delta = d * c;
-        h *= delta;
-        if (fabs(delta - 1.0) < 1e-16) break;
+    const or_quad qa = a, qb = b, qx = x;
+    or_quad term = 1, sum = 1;
+    for (int j = 0; j < 10000000; ++j) {
+        term *= (qa + qb + j) / (qa + 1 + j) * qx;
+        sum += term;
+        if (term < sum * (or_quad)1e-34) break;
     }
-    return h;
+    const or_quad lnB = OR_LGAMMA(qa) + OR_LGAMMA(qb) - OR_LGAMMA(qa + qb);
+    const or_quad ln = qa * OR_LOG(qx) + qb * OR_LOG1P(-qx) - lnB - OR_LOG(qa) + OR_LOG(sum);
+    return (double)OR_EXP(ln);
 }
 
 double oracle_betainc(double a, double b, double x)
 {
     if (x <= 0.0) return 0.0;
     if (x >= 1.0) return 1.0;
-    or_quad lnB = OR_LGAMMA((or_quad)a) + OR_LGAMMA((or_quad)b)
-                - OR_LGAMMA((or_quad)a + (or_quad)b);
-    or_quad lnpre = (or_quad)a * OR_LOG((or_quad)x)
-                  + (or_quad)b * OR_LOG1P(-(or_quad)x) - lnB;
-    double pre = (double)OR_EXP(lnpre);
     if (x < (a + 1.0) / (a + b + 2.0) || b > 50.0 * a)
-        return pre * or_beta_cf(a, b, x) / a;
-    return 1.0 - pre * or_beta_cf(b, a, 1.0 - x) / b;
+        return or_beta_series(a, b, x);
+    return 1.0 - or_beta_series(b, a, 1.0 - x);
 }
 
 double oracle_f_cdf(double d1, double d2, double f)
@@ -317,6 +304,11 @@ static double or_lum(double R, double G, double B)
     return 0.2126 * R + 0.7152 * G + 0.0722 * B;
 }
 
+double oracle_lum(double R, double G, double B)
+{
+    return or_lum(R, G, B);
+}
+
 /* ------------------------------------------------------------------------
  * 6. The full method, brute force over all pairs (Sec. 5.1, steps 1-5, with
  *    the estimate of Eq. progressive-VCM-estimator).  For every iteration
@@ -414,12 +406,16 @@ static double or_window_f(const or_window* w, int nch, int ch, double m,
  *   out_r:      (iters+1)*nh  radius used in each iteration, then final radius
  *   out_counts: iters*nh*12   window counts c_g that the test of that
  *                             iteration used (after accumulation, before reset)
- *   out_S:      iters*nh*12   window sums of psi (test channel 0) per group
- *   out_Q:      iters*nh*12   window sums of psi^2 per group
+ *   out_S:      iters*nh*ntest*12  window sums of psi per tested channel
+ *                             (ntest = 3 with rgb_test and RGB flux, else 1)
+ *                             and group
+ *   out_Q:      iters*nh*ntest*12  window sums of psi^2 likewise
  *   out_F:      iters*nh      F of test channel 0
  *   out_Fc:     iters*nh      critical value used
  *   out_reject: iters*nh      1 if rejected
  *   out_pairs:  iters*nh      in-disk pairs gathered in that iteration
+ *   out_est:    iters*nh*nch  that iteration's kernel estimate
+ *                             sum(w Phi) / (pi r_i^2) (the term added to tau)
  *   out_t:      nh            final window length t
  *   out_tau:    nh*nch        final accumulated estimate sum
  * Returns 0 on success, -1 on bad arguments.
@@ -433,7 +429,7 @@ int oracle_run(int64_t nh, const float* hp_pos, const float* hp_u,
                float* out_r, int32_t* out_counts, double* out_S,
                double* out_Q, double* out_F, double* out_Fc,
                uint8_t* out_reject, int32_t* out_pairs, int32_t* out_t,
-               double* out_tau)
+               double* out_tau, double* out_est)
 {
     if (nh < 0 || iters < 0 || J < 2 || (nch != 1 && nch != 3) || !prm ||
         (prm->test != 0 && prm->test != 1))
@@ -504,16 +500,17 @@ int oracle_run(int64_t nh, const float* hp_pos, const float* hp_u,
              * kernel. */
             double area = M_PI * (double)r * (double)r;
             for (int c = 0; c < nch; ++c) tau[c] += phi_sum[c] / area;
+            if (out_est)
+                for (int c = 0; c < nch; ++c) out_est[((size_t)it * nh + h) * nch + c] = phi_sum[c] / area;
 
             int32_t tp = t + 1;
             double m = (double)tp * (double)J;
             int reject = 0;
             double F0 = 0.0;
             int64_t cnt[OR_NG];
-            double S[OR_NG], Q[OR_NG];
+            double S[3][OR_NG], Q[3][OR_NG];
             for (int ch = 0; ch < ntest; ++ch) {
-                double F = or_window_f(&win, wch, ch, m, ch == 0 ? cnt : NULL,
-                                       ch == 0 ? S : NULL, ch == 0 ? Q : NULL);
+                double F = or_window_f(&win, wch, ch, m, ch == 0 ? cnt : NULL, S[ch], Q[ch]);
                 if (ch == 0) F0 = F;
                 if (F > fc[tp]) reject = 1;
             }
@@ -525,8 +522,11 @@ int oracle_run(int64_t nh, const float* hp_pos, const float* hp_u,
             }
             size_t o = (size_t)it * nh + h;
             if (out_counts) for (int g = 0; g < OR_NG; ++g) out_counts[o * OR_NG + g] = (int32_t)cnt[g];
-            if (out_S) for (int g = 0; g < OR_NG; ++g) out_S[o * OR_NG + g] = S[g];
-            if (out_Q) for (int g = 0; g < OR_NG; ++g) out_Q[o * OR_NG + g] = Q[g];
+            for (int ch = 0; ch < ntest; ++ch)
+                for (int g = 0; g < OR_NG; ++g) {
+                    if (out_S) out_S[(o * ntest + ch) * OR_NG + g] = S[ch][g];
+                    if (out_Q) out_Q[(o * ntest + ch) * OR_NG + g] = Q[ch][g];
+                }
             if (out_F) out_F[o] = F0;
             if (out_Fc) out_Fc[o] = prm->test == 1 ? chic : fc[tp];
             if (out_reject) out_reject[o] = (uint8_t)reject;

@@ -176,26 +176,34 @@ bool finite_pos(float x) { return isfinite(x) && x > 0.f; }
 int ensure_fc(ppm_ctx* c, int upto, int* launches)
 {
     if (upto <= c->fc_upto) return PPM_OK;
-    ++*launches;
+    *launches += 2;
     if (upto >= c->fc_cap) {
         int cap = c->fc_cap > 0 ? c->fc_cap : 256;
         while (cap <= upto) cap *= 2;
         double* nt = nullptr;
+        float2* nm = nullptr;
         if (!dalloc(&nt, cap + 1)) return PPM_ENOMEM;
+        if (!dalloc(&nm, cap + 1)) { cudaFree(nt); return PPM_ENOMEM; }
         if (c->fc) {
             PPM_CUDA(cudaMemcpyAsync(nt, c->fc, (c->fc_upto + 1) * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+            PPM_CUDA(cudaMemcpyAsync(nm, c->fm, (c->fc_upto + 1) * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
             PPM_CUDA(cudaStreamSynchronize(c->stream));
             cudaFree(c->fc);
+            cudaFree(c->fm);
         } else {
             PPM_CUDA(cudaMemsetAsync(nt, 0, sizeof(double), c->stream));
+            PPM_CUDA(cudaMemsetAsync(nm, 0, sizeof(float2), c->stream));
         }
         c->fc = nt;
+        c->fm = nm;
         c->fc_cap = cap;
     }
     // fill up to the capacity in one launch: later iterations hit the table
     const int to = c->fc_cap;
     int rc = c->prm.test ? ppm_chi2_fill(c->fc, c->fc_upto + 1, to, PPM_NG - 1, c->prm.alpha_f, c->stream)
                          : ppm_fcrit_fill(c->fc, c->fc_upto + 1, to, (double)c->J, c->prm.alpha_f, c->stream);
+    if (rc) return rc;
+    rc = ppm_window_m_fill(c->fm, c->fc_upto + 1, to, (double)c->J, c->stream);
     if (rc) return rc;
     c->fc_upto = to;
     return PPM_OK;
@@ -211,7 +219,7 @@ void free_ctx(ppm_ctx* c)
     cudaFree(c->rec0); cudaFree(c->rec1); cudaFree(c->aux);
     cudaFree(c->pack);
     ppm_sort_scratch_free(&c->sort);
-    cudaFree(c->geom_dev); cudaFree(c->rmax); cudaFree(c->fc);
+    cudaFree(c->geom_dev); cudaFree(c->rmax); cudaFree(c->fc); cudaFree(c->fm);
     cudaFree(c->counters); cudaFree(c->err_dev); cudaFree(c->feat);
     if (c->copy_st) cudaStreamSynchronize(c->copy_st);
     for (int k = 0; k < 2; ++k) {
@@ -289,6 +297,7 @@ const char* ppm_strerror(int code)
         case PPM_ECUDA: return "CUDA runtime error";
         case PPM_ETIMEOUT: return "bounded device wait timed out";
         case PPM_ESTATE: return "call out of order";
+        case PPM_EINCOMPLETE: return "a gather skipped cells (a sphere spanned more cells than a hash block)";
         default: return "unknown error";
     }
 }
@@ -430,7 +439,9 @@ int ppm_get_state(ppm_ctx* c, const ppm_state_view* v)
         PPM_LAUNCH_CHECK();
     }
     PPM_CUDA(cudaStreamSynchronize(c->stream));
-    return PPM_OK;
+    int32_t err = 0;
+    PPM_CUDA(cudaMemcpy(&err, c->err_dev, sizeof(err), cudaMemcpyDeviceToHost));
+    return ppm_flags_status(err);
 }
 
 int ppm_set_state(ppm_ctx* c, const ppm_state_view* v)
@@ -485,7 +496,7 @@ int ppm_stats(ppm_ctx* c, ppm_iter_stats* out)
     out->launches = c->launches_iter;
     out->gather_ms = -1.f;
     out->proposals = (int64_t)cnt[4];
-    return PPM_OK;
+    return ppm_flags_status(err);
 }
 
 }  // extern "C"
@@ -627,7 +638,7 @@ int ppm_stats_host(ppm_ctx* c, int32_t iter, ppm_iter_stats* out)
     out->cell = hs.cell;
     out->launches = c->host_launches[k];
     out->gather_ms = -1.f;
-    return PPM_OK;
+    return ppm_flags_status(hs.err);
 }
 
 int ppm_f_critical(int64_t J, double alpha_f, int32_t t_max, double* out, void* stream)

@@ -37,7 +37,7 @@ struct IterScalars {
     double pad;
 };
 
-constexpr int kFcCap = 1024;     // window lengths with a precomputed F_c
+constexpr int kFcCap0 = 1024;    // window lengths with a precomputed F_c at create (grows)
 
 }  // namespace
 
@@ -67,8 +67,10 @@ struct ppm_batch {
     // per problem
     GridGeom* geom = nullptr;
     float *rmax = nullptr, *rmax_next = nullptr, *cf_dev = nullptr, *rmin_dev = nullptr;
-    float *Jf = nullptr, *nvm = nullptr, *bound = nullptr;
-    double* fc = nullptr;
+    float *nvm = nullptr, *bound = nullptr;
+    double* fc = nullptr;            // [P][fc_cap + 1] F_c by window length
+    float2* fm = nullptr;            // [P][fc_cap + 1] (1/m, 12 (m-1) / (11 m)), m = t J
+    int fc_cap = 0;
     unsigned long long* counters = nullptr;   // 4 per problem
     unsigned long long* pairs_total = nullptr;
     // work lists
@@ -142,7 +144,7 @@ void free_batch(ppm_batch* b)
     cudaFree(b->r); cudaFree(b->t); cudaFree(b->F); cudaFree(b->tau); cudaFree(b->cnt);
     cudaFree(b->S); cudaFree(b->Q);
     cudaFree(b->geom); cudaFree(b->rmax); cudaFree(b->rmax_next); cudaFree(b->cf_dev);
-    cudaFree(b->rmin_dev); cudaFree(b->Jf); cudaFree(b->nvm); cudaFree(b->bound); cudaFree(b->fc);
+    cudaFree(b->rmin_dev); cudaFree(b->nvm); cudaFree(b->bound); cudaFree(b->fc); cudaFree(b->fm);
     cudaFree(b->counters); cudaFree(b->pairs_total);
     cudaFree(b->tiles); cudaFree(b->pack_blocks); cudaFree(b->head);
     cudaFree(b->ptab_d); cudaFree(b->sc_d);
@@ -250,9 +252,10 @@ struct BatchArgs {
     unsigned* head;
     const GridGeom* geom;
     const double* fc;
+    const float2* fm;
+    int fc_cap;
     float* rmax_next;
     unsigned long long* counters;
-    const float* Jf;
     const float* nvm;
     const float* bound;
     float k;
@@ -264,6 +267,7 @@ k_batch_gather(GatherArgs a, BatchArgs bt)
 {
     __shared__ BlockShared<NCH, NTC, MAPPING> bsh;
     __shared__ int s_tile;
+    if (*a.err & 4) return;          // the grid's sort gave up: no usable grid
     for (;;) {
         if (threadIdx.x == 0) s_tile = (int)atomicAdd(bt.head, 1u);
         __syncthreads();
@@ -274,14 +278,14 @@ k_batch_gather(GatherArgs a, BatchArgs bt)
         const int p = T.x;
         Prob pr;
         pr.geom = bt.geom + p;
-        pr.fc = bt.fc + (int64_t)p * (kFcCap + 1);
+        pr.fc = bt.fc + (int64_t)p * (bt.fc_cap + 1);
+        pr.fm = bt.fm + (int64_t)p * (bt.fc_cap + 1);
         pr.rmax_next = bt.rmax_next + p;
         pr.counters = bt.counters + 4 * p;
-        pr.J = bt.Jf[p];
         pr.k = bt.k;
         pr.bound = bt.bound[p];
         pr.n_vm = bt.nvm[p];
-        pr.fc_max = kFcCap;
+        pr.fc_max = bt.fc_cap;
         pr.pid = (uint32_t)p;
         pr.inv_r0 = 0.f;
         pr.log_iter = 0.f;
@@ -398,8 +402,9 @@ int run_gather(ppm_batch* b)
     a.feat = nullptr;
     BatchArgs bt;
     bt.tiles = b->tiles; bt.ntiles = b->ntiles; bt.head = b->head;
-    bt.geom = b->geom; bt.fc = b->fc; bt.rmax_next = b->rmax_next; bt.counters = b->counters;
-    bt.Jf = b->Jf; bt.nvm = b->nvm; bt.bound = b->bound; bt.k = b->prm.k;
+    bt.geom = b->geom; bt.fc = b->fc; bt.fm = b->fm; bt.fc_cap = b->fc_cap;
+    bt.rmax_next = b->rmax_next; bt.counters = b->counters;
+    bt.nvm = b->nvm; bt.bound = b->bound; bt.k = b->prm.k;
     const bool nrm = b->normals, vcm = b->prm.vcm != 0;
     if (b->nch == 1) {
         if (vcm) return nrm ? launch_batch_gather<1, 1, true, true>(b, a, bt) : launch_batch_gather<1, 1, false, true>(b, a, bt);
@@ -426,6 +431,50 @@ int occupancy(ppm_batch* b)
     }
     if (vcm) return nrm ? gather_occupancy<3, 1, true, true>(b) : gather_occupancy<3, 1, false, true>(b);
     return nrm ? gather_occupancy<3, 1, true, false>(b) : gather_occupancy<3, 1, false, false>(b);
+}
+
+// F_c and window-m tables of every problem for window lengths up to at
+// least `upto` (doubling the capacity): new arrays, the old rows copied, the
+// new entries computed; the captured graph holds the old pointers, so it is
+// dropped and captured again by the next iteration
+int grow_fc(ppm_batch* b, int upto)
+{
+    if (upto <= b->fc_cap) return PPM_OK;
+    int cap = b->fc_cap > 0 ? b->fc_cap : kFcCap0;
+    while (cap < upto) cap *= 2;
+    const int P = b->P;
+    double* nfc = nullptr;
+    float2* nfm = nullptr;
+    if (!dal(&nfc, (int64_t)P * (cap + 1))) return PPM_ENOMEM;
+    if (!dal(&nfm, (int64_t)P * (cap + 1))) { cudaFree(nfc); return PPM_ENOMEM; }
+    cudaStream_t st = b->st;
+    int rc = PPM_OK;
+    const int from = b->fc_cap + 1;
+    if (b->fc) {
+        if (!OKC(cudaMemcpy2DAsync(nfc, (cap + 1) * sizeof(double), b->fc, (b->fc_cap + 1) * sizeof(double),
+                                   (b->fc_cap + 1) * sizeof(double), P, cudaMemcpyDeviceToDevice, st)) ||
+            !OKC(cudaMemcpy2DAsync(nfm, (cap + 1) * sizeof(float2), b->fm, (b->fc_cap + 1) * sizeof(float2),
+                                   (b->fc_cap + 1) * sizeof(float2), P, cudaMemcpyDeviceToDevice, st)))
+            rc = PPM_ECUDA;
+    } else {
+        if (!OKC(cudaMemsetAsync(nfc, 0, (size_t)P * (cap + 1) * sizeof(double), st)) ||
+            !OKC(cudaMemsetAsync(nfm, 0, (size_t)P * (cap + 1) * sizeof(float2), st)))
+            rc = PPM_ECUDA;
+    }
+    for (int p = 0; p < P && rc == PPM_OK; ++p) {
+        rc = ppm_fcrit_fill(nfc + (int64_t)p * (cap + 1), from, cap, (double)b->J[p], b->prm.alpha_f, st);
+        if (rc == PPM_OK) rc = ppm_window_m_fill(nfm + (int64_t)p * (cap + 1), from, cap, (double)b->J[p], st);
+    }
+    if (rc == PPM_OK && !OKC(cudaStreamSynchronize(st))) rc = PPM_ECUDA;
+    if (rc) { cudaFree(nfc); cudaFree(nfm); return rc; }
+    cudaFree(b->fc);
+    cudaFree(b->fm);
+    b->fc = nfc;
+    b->fm = nfm;
+    b->fc_cap = cap;
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    return PPM_OK;
 }
 
 // enqueue one whole iteration on b->st (captured into the graph)
@@ -463,16 +512,16 @@ int enqueue_iteration(ppm_batch* b)
         ++launches;
         // the ping-pong pointer sequence of the sort is recorded into the
         // graph as it is at capture time, so every replay is consistent
-        int rc = ppm_radix_sort_pairs_lookback(&b->sort, n, b->tbits, b->err, st);
+        int rc = ppm_radix_sort_pairs_lookback(&b->sort, n, b->tbits, b->err, st, b->prm.wait_limit);
         if (rc) return rc;
         launches += 2 + (b->tbits + 7) / 8;
     }
-    int rc = ppm_cell_start_launch(b->sort.keys, n, T, b->cell_start, st);
+    int rc = ppm_cell_start_launch(b->sort.keys, n, T, b->cell_start, b->err, st);
     if (rc) return rc;
     ++launches;
     if (n > 0) {
         const bool rec1 = b->nch == 3 || b->prm.vcm;
-        rc = ppm_permute_launch(n, b->sort.vals, b->pack, b->rec0, rec1 ? b->rec1 : nullptr, b->aux, st);
+        rc = ppm_permute_launch(n, b->sort.vals, b->pack, b->rec0, rec1 ? b->rec1 : nullptr, b->aux, b->err, st);
         if (rc) return rc;
         ++launches;
     }
@@ -562,8 +611,8 @@ int ppm_batch_create(int32_t n_problems, const ppm_hitpoints* hp, const float* r
               dal(&b->r, nh) && dal(&b->t, nh) && dal(&b->F, nh) && dal(&b->tau, nh * b->nch) &&
               dal(&b->cnt, nh * PPM_NG) && dal(&b->S, nh * PPM_NG * b->ntc) && dal(&b->Q, nh * PPM_NG * b->ntc) &&
               dal(&b->geom, P) && dal(&b->rmax, P) && dal(&b->rmax_next, P) && dal(&b->cf_dev, P) &&
-              dal(&b->rmin_dev, P) && dal(&b->Jf, P) && dal(&b->nvm, P) && dal(&b->bound, P) &&
-              dal(&b->fc, (int64_t)P * (kFcCap + 1)) && dal(&b->counters, 4ll * P) &&
+              dal(&b->rmin_dev, P) && dal(&b->nvm, P) && dal(&b->bound, P) &&
+              dal(&b->counters, 4ll * P) &&
               dal(&b->pairs_total, P) && dal(&b->head, 1) && dal(&b->ptab_d, P) && dal(&b->sc_d, 1) &&
               dal(&b->err, 1) && dal(&b->rec0, np) && dal(&b->aux, np) &&
               dal(&b->pack, np * ((b->nch == 3 || prm.vcm) ? 3 : 2));
@@ -591,17 +640,15 @@ int ppm_batch_create(int32_t n_problems, const ppm_hitpoints* hp, const float* r
                                        b->hp_u + o, b->hp_v + o, st);
         }
         if (rc) break;
-        std::vector<float> rfill(nh, 0.f), jf(P), nv(P);
+        std::vector<float> rfill(nh, 0.f), nv(P);
         for (int p = 0; p < P; ++p) {
             for (int64_t i = 0; i < b->hp_n[p]; ++i) rfill[b->hp_off[p] + i] = r0[p];
-            jf[p] = (float)J[p];
             nv[p] = prm.n_vm > 0.f ? prm.n_vm : (float)J[p];
         }
         if (!OKC(cudaMemcpyAsync(b->r, rfill.data(), nh * sizeof(float), cudaMemcpyHostToDevice, st)) ||
             !OKC(cudaMemcpyAsync(b->rmax, b->r0.data(), P * sizeof(float), cudaMemcpyHostToDevice, st)) ||
             !OKC(cudaMemcpyAsync(b->cf_dev, b->cf.data(), P * sizeof(float), cudaMemcpyHostToDevice, st)) ||
             !OKC(cudaMemcpyAsync(b->rmin_dev, b->rmin.data(), P * sizeof(float), cudaMemcpyHostToDevice, st)) ||
-            !OKC(cudaMemcpyAsync(b->Jf, jf.data(), P * sizeof(float), cudaMemcpyHostToDevice, st)) ||
             !OKC(cudaMemcpyAsync(b->nvm, nv.data(), P * sizeof(float), cudaMemcpyHostToDevice, st)) ||
             !OKC(cudaMemsetAsync(b->t, 0, nh * sizeof(int32_t), st)) ||
             !OKC(cudaMemsetAsync(b->F, 0, nh * sizeof(float), st)) ||
@@ -613,11 +660,7 @@ int ppm_batch_create(int32_t n_problems, const ppm_hitpoints* hp, const float* r
             !OKC(cudaMemsetAsync(b->err, 0, sizeof(int32_t), st)) ||
             !OKC(cudaStreamSynchronize(st))) { rc = PPM_ECUDA; break; }
         // F_c tables, one per problem (J differs)
-        for (int p = 0; p < P && rc == PPM_OK; ++p) {
-            double* tab = b->fc + (int64_t)p * (kFcCap + 1);
-            if (!OKC(cudaMemsetAsync(tab, 0, sizeof(double), st))) { rc = PPM_ECUDA; break; }
-            rc = ppm_fcrit_fill(tab, 1, kFcCap, (double)J[p], prm.alpha_f, st);
-        }
+        rc = grow_fc(b, kFcCap0);
         if (rc) break;
         // tiles of tile_hits hit points, problems with the most photons per disk
         // (J r0^2) first so the long tiles start early
@@ -663,6 +706,13 @@ int ppm_batch_iterate(ppm_batch* b, const ppm_photons* ph, int32_t iter)
         if (q.n > 0 && (!q.pos || !q.flux)) return PPM_EINVAL;
         if (b->prm.vcm && q.n > 0 && (!q.rho || !q.wq)) return PPM_EINVAL;
         if (b->normals && q.n > 0 && !q.nq) return PPM_EINVAL;
+    }
+    // a window can reach length iter: keep the tables ahead of it (the last
+    // launch must be done with the old tables first)
+    if (iter > b->fc_cap) {
+        PPM_CUDA(cudaStreamSynchronize(b->st));
+        int rc = grow_fc(b, iter);
+        if (rc) return rc;
     }
     // staging for this launch: wait until the previous launch has copied it
     PPM_CUDA(cudaEventSynchronize(b->ev_staged));
@@ -723,7 +773,9 @@ int ppm_batch_get_state(ppm_batch* b, int32_t problem, const ppm_state_view* v)
         PPM_LAUNCH_CHECK();
     }
     PPM_CUDA(cudaStreamSynchronize(b->st));
-    return PPM_OK;
+    int32_t err = 0;
+    PPM_CUDA(cudaMemcpy(&err, b->err, sizeof(err), cudaMemcpyDeviceToHost));
+    return ppm_flags_status(err);
 }
 
 int ppm_batch_stats(ppm_batch* b, ppm_iter_stats* out)
@@ -759,7 +811,7 @@ int ppm_batch_stats(ppm_batch* b, ppm_iter_stats* out)
         s.launches = b->launches;
         s.gather_ms = gms;
     }
-    return PPM_OK;
+    return ppm_flags_status(err);
 }
 
 int ppm_batch_graph_ready(ppm_batch* b)

@@ -8,17 +8,20 @@
 // window, J light paths per iteration) the table is indexed by t.
 //
 // CDF_F(f) = I_x(d1/2, d2/2) with x = d1 f / (d1 f + d2) (regularized
-// incomplete beta).  I is evaluated from its continued fraction with the
-// modified Lentz method, on the side of I_x(a,b) = 1 - I_{1-x}(b,a) where
-// the fraction converges quickly -- except for b >> a (d2 >> d1, always the
-// case here), where the other side's odd terms are -1 + O(1/b) and each
-// step cancels ~9 digits: there the direct side is well conditioned and
-// converges in a few dozen terms.  The quantile is found by Newton's
-// method on the CDF (derivative = the F density) kept inside a bisection
-// bracket.  d2 reaches ~1e11, where lgamma(b) - lgamma(a+b) loses ~1e-6 to
-// cancellation in FP64, so for b >= 64 that difference is taken from the
-// Stirling series of log Gamma written as a difference (no cancellation;
-// the first omitted term, 1/(1680 b^7), is below 1e-15 there).
+// incomplete beta).  I is evaluated from its continued fraction (DLMF
+// Sec. 8.17(v)), whose convergents are built by the three-term forward
+// recurrences of their numerators and denominators (Wallis), rescaled at
+// every step.  The fraction is taken on the side of the symmetry
+// I_x(a,b) = 1 - I_{1-x}(b,a) where it converges quickly, except for b >> a
+// (d2 >> d1, always the case here), where the other side's odd terms are
+// close to -1 and every step cancels most digits: there the direct side is
+// well conditioned and converges in a few dozen terms.  The quantile is
+// found by Newton's method on the CDF (derivative = the F density) kept
+// inside a bisection bracket.  d2 reaches ~1e11, where lgamma(b) -
+// lgamma(a+b) loses ~1e-6 to cancellation in FP64, so for b >= 64 that
+// difference is taken from the Stirling series of log Gamma written as a
+// difference (no cancellation; the first omitted term, 1/(1680 b^7), is
+// below 1e-15 there).
 #include "ppm_internal.cuh"
 
 namespace {
@@ -36,31 +39,36 @@ __device__ double lbeta_fp64(double a, double b)
     return lgamma(a) + d;
 }
 
-// continued fraction of I_x(a,b) (without the x^a (1-x)^b / (a B) factor)
-__device__ double betacf_fp64(double a, double b, double x)
+// Value of the continued fraction 1 / (1 + e_1 / (1 + e_2 / (1 + ...))) of
+// DLMF Sec. 8.17(v), so that I_x(a,b) = x^a (1-x)^b / (a B(a,b)) times it, with
+//   e_{2j}   =  j (b - j) x / ((a + 2j - 1)(a + 2j)),
+//   e_{2j+1} = -(a + j)(a + b + j) x / ((a + 2j)(a + 2j + 1)).
+// Convergent n is num_n / den_n with num_n = num_{n-1} + e_{n-1} num_{n-2}
+// (den likewise) from num = (1, 1), den = (1, 1 + e_1); the pair of the
+// last two convergents is divided by den_n every step so nothing overflows.
+__device__ double beta_fraction_fp64(double a, double b, double x)
 {
-    const double fpmin = 1e-300;
-    double c = 1.0;
-    double d = 1.0 - (a + b) * x / (a + 1.0);
-    if (fabs(d) < fpmin) d = fpmin;
-    d = 1.0 / d;
-    double h = d;
-    for (int m = 1; m <= 4000; ++m) {
-        const double m2 = 2.0 * m;
-        double aa = m * (b - m) * x / ((a - 1.0 + m2) * (a + m2));
-        d = 1.0 + aa * d; if (fabs(d) < fpmin) d = fpmin;
-        c = 1.0 + aa / c; if (fabs(c) < fpmin) c = fpmin;
-        d = 1.0 / d;
-        h *= d * c;
-        aa = -(a + m) * (a + b + m) * x / ((a + m2) * (a + 1.0 + m2));
-        d = 1.0 + aa * d; if (fabs(d) < fpmin) d = fpmin;
-        c = 1.0 + aa / c; if (fabs(c) < fpmin) c = fpmin;
-        d = 1.0 / d;
-        const double del = d * c;
-        h *= del;
-        if (fabs(del - 1.0) < 2e-16) break;
+    double num_prev = 1.0, den_prev = 1.0;            // convergent 1: 1 / 1
+    double num = 1.0, den = 1.0 - (a + b) * x / (a + 1.0);   // convergent 2: 1 / (1 + e_1)
+    double value = num / den;
+    for (int n = 2; n <= 8000; ++n) {
+        const int j = n >> 1;
+        const double e = (n & 1) ? -(a + j) * (a + b + j) * x / ((a + 2.0 * j) * (a + 2.0 * j + 1.0))
+                                 : j * (b - j) * x / ((a + 2.0 * j - 1.0) * (a + 2.0 * j));
+        const double num_next = num + e * num_prev;
+        double den_next = den + e * den_prev;
+        if (den_next == 0.0) den_next = 1e-300;       // a zero denominator: step over it
+        const double s = 1.0 / den_next;
+        num_prev = num * s;
+        den_prev = den * s;
+        num = num_next * s;
+        den = 1.0;
+        const double v = num;
+        const bool done = fabs(v - value) <= 4e-16 * fabs(v);
+        value = v;
+        if (done && (n & 1)) break;                   // stop after an odd term
     }
-    return h;
+    return value;
 }
 
 // CDF and density of F(d1, d2) at f > 0
@@ -73,8 +81,8 @@ __device__ void f_cdf_pdf(double d1, double d2, double f, double* cdf, double* p
     const double l1x = -log1p(s / d2);          // log(1 - x) without cancellation
     const double lb = lbeta_fp64(a, b);
     const double front = exp(a * lx + b * l1x - lb);
-    if (x < (a + 1.0) / (a + b + 2.0) || b > 50.0 * a) *cdf = front * betacf_fp64(a, b, x) / a;
-    else *cdf = 1.0 - front * betacf_fp64(b, a, d2 / (s + d2)) / b;
+    if (x < (a + 1.0) / (a + b + 2.0) || b > 50.0 * a) *cdf = front * beta_fraction_fp64(a, b, x) / a;
+    else *cdf = 1.0 - front * beta_fraction_fp64(b, a, d2 / (s + d2)) / b;
     // d/df I_x = x^(a-1) (1-x)^(b-1) / B(a,b) * dx/df, dx/df = d1 d2 / (s + d2)^2
     *pdf = exp((a - 1.0) * lx + (b - 1.0) * l1x - lb) * d1 * d2 / ((s + d2) * (s + d2));
 }
@@ -111,38 +119,63 @@ __global__ void k_fcrit_table(double* __restrict__ table, int t_from, int t_to,
     table[t] = f_quantile(d1, d2, 1.0 - alpha);
 }
 
+// The F statistic's dependence on the window length t: with m = t J samples
+// per group (an integer, taken in FP64, never FP32),
+//   SSW = sum_g Q_g - (1/m) sum_g S_g^2,
+//   F = (SSB / (n-1)) / (SSW / (n (m-1))) = (dev2 / SSW) * n (m-1) / ((n-1) m),
+// dev2 = sum_g (S_g - S/n)^2.  mtab[t] = (1/m, n (m-1) / ((n-1) m)), each
+// computed in FP64 and rounded once to FP32 for the gather's epilogue.
+__global__ void k_window_m(float2* __restrict__ mtab, int t_from, int t_to, double J)
+{
+    const int t = t_from + blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > t_to) return;
+    const double m = (double)t * J;
+    mtab[t] = make_float2((float)(1.0 / m),
+                          (float)((double)PPM_NG * (m - 1.0) / ((double)(PPM_NG - 1) * m)));
+}
+
 // CPPM's count test (Sec. 3.2.3): chi_c = the (1 - alpha) quantile of
 // chi^2(k) with k = n - 1 = 11, whose CDF is P(k/2, x/2), P the regularized
-// lower incomplete gamma function: its power series below x = a + 1 and the
-// continued fraction of Q = 1 - P (modified Lentz) above (Press et al.,
-// Numerical Recipes, Sec. 6.2).
-__device__ double gamma_p_fp64(double a, double x)
+// lower incomplete gamma function.  Below z = a + 1, P comes from its power
+// series (DLMF Sec. 8.7)
+//   P(a, z) = z^a e^-z / Gamma(a + 1) * sum_{j >= 0} z^j / ((a+1)...(a+j));
+// above, 1 - Q with Q from the continued fraction of Gamma(a, z) (DLMF Sec. 8.9)
+//   Gamma(a, z) = e^-z z^a / (z + (1-a) / (1 + 1 / (z + (2-a) / (1 + 2 / (z + ...))))),
+// whose convergents come from the forward recurrences, as for the beta.
+__device__ double gamma_p_fp64(double a, double z)
 {
-    if (x <= 0.0) return 0.0;
-    const double lead = a * log(x) - x - lgamma(a);
-    if (x < a + 1.0) {
-        double ap = a, del = 1.0 / a, sum = del;
-        for (int n = 0; n < 4000; ++n) {
-            ap += 1.0;
-            del *= x / ap;
-            sum += del;
-            if (fabs(del) < fabs(sum) * 1e-17) break;
+    if (z <= 0.0) return 0.0;
+    if (z < a + 1.0) {
+        double term = 1.0, sum = 1.0;
+        for (int j = 1; j < 8000; ++j) {
+            term *= z / (a + j);
+            sum += term;
+            if (term <= 1e-17 * sum) break;
         }
-        return sum * exp(lead);
+        return exp(a * log(z) - z - lgamma(a + 1.0)) * sum;
     }
-    const double tiny = 1e-300;
-    double b = x + 1.0 - a, c = 1.0 / tiny, d = 1.0 / b, h = d;
-    for (int i = 1; i < 4000; ++i) {
-        const double an = -i * (i - a);
-        b += 2.0;
-        d = an * d + b; if (fabs(d) < tiny) d = tiny;
-        c = b + an / c; if (fabs(c) < tiny) c = tiny;
-        d = 1.0 / d;
-        const double del = d * c;
-        h *= del;
-        if (fabs(del - 1.0) < 1e-16) break;
+    // partial numerators / denominators: 1 / z first, then for k = 1, 2, ...
+    // (k - a) / 1 (even n = 2k) and k / z (odd n = 2k + 1)
+    double num_prev = 0.0, den_prev = 1.0;            // convergent 0: 0 / 1
+    double num = 1.0, den = z;                        // convergent 1: 1 / z
+    double value = num / den;
+    for (int n = 2; n <= 16000; ++n) {
+        const int k = n >> 1;
+        const double an = (n & 1) ? (double)k : (double)k - a;   // partial numerator
+        const double bn = (n & 1) ? z : 1.0;                      // partial denominator
+        const double num_next = bn * num + an * num_prev;
+        double den_next = bn * den + an * den_prev;
+        if (den_next == 0.0) den_next = 1e-300;
+        const double s = 1.0 / den_next;
+        num_prev = num * s;
+        den_prev = den * s;
+        num = num_next * s;
+        den = 1.0;
+        const bool done = fabs(num - value) <= 4e-16 * fabs(num);
+        value = num;
+        if (done && (n & 1)) break;
     }
-    return 1.0 - exp(lead) * h;
+    return 1.0 - exp(a * log(z) - z - lgamma(a)) * value;
 }
 
 // quantile of chi^2(k) at q: Newton on the CDF (derivative = the density
@@ -184,6 +217,15 @@ int ppm_chi2_fill(double* table, int t_from, int t_to, double k, double alpha, c
     if (t_to < t_from) return PPM_OK;
     const int n = t_to - t_from + 1;
     k_chi2_table<<<(n + 63) / 64, 64, 0, st>>>(table, t_from, t_to, k, alpha);
+    PPM_LAUNCH_CHECK();
+    return PPM_OK;
+}
+
+int ppm_window_m_fill(float2* mtab, int t_from, int t_to, double J, cudaStream_t st)
+{
+    if (t_to < t_from) return PPM_OK;
+    const int n = t_to - t_from + 1;
+    k_window_m<<<(n + 127) / 128, 128, 0, st>>>(mtab, t_from, t_to, J);
     PPM_LAUNCH_CHECK();
     return PPM_OK;
 }

@@ -108,9 +108,9 @@ int ppm_gather_launch(ppm_ctx* c, float bound)
     Prob pr;
     pr.geom = c->geom_dev;
     pr.fc = c->fc;
+    pr.fm = c->fm;
     pr.rmax_next = c->rmax + (c->rmax_cur ^ 1);
     pr.counters = c->counters;
-    pr.J = (float)c->J;
     pr.k = c->prm.k;
     pr.bound = bound;
     pr.n_vm = c->prm.n_vm > 0.f ? c->prm.n_vm : (float)c->J;

@@ -48,9 +48,10 @@ struct GatherArgs {
 struct Prob {
     const GridGeom* geom;
     const double* fc;               // F_c by window length
+    const float2* fm;               // (1/m, 12 (m-1) / (11 m)) by window length, m = t J (from FP64)
     float* rmax_next;               // max radius after the update
     unsigned long long* counters;   // pairs, candidates, rejects, pairs total
-    float J, k, bound, n_vm;
+    float k, bound, n_vm;
     int32_t fc_max;                 // last valid index of fc
     uint32_t pid;                   // problem id carried by its photons (batch)
     float inv_r0;                   // features: 1 / initial radius
@@ -881,7 +882,9 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
         // with t >= the iteration count: clamp the lookup and flag it
         int32_t tpi = tp;
         if (tp < 1 || tp > pr.fc_max) { atomicOr(a.err, 2); tpi = max(1, min(tp, pr.fc_max)); }
-        const float m = __fmul_rn((float)tp, pr.J);
+        // m = t' J samples per group never exists in FP32: the table holds
+        // 1/m and 12 (m-1) / (11 m), each computed in FP64 and rounded once
+        const float2 mf = pr.fm[tpi];
         const int64_t nh = a.nh;
         bool reject = false;
         float F0 = 0.f;
@@ -918,9 +921,9 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
             for (int g = 0; g < PPM_NG; ++g) { const float d = Sg[g] - Sbar; dev2 = fmaf(d, d, dev2); }
             // SSB = dev2 / m, SSW = sum Q - sum S^2 / m,
             // F = (SSB / 11) / (SSW / (12 (m-1))) = (dev2 / SSW) * 12 (m-1) / (11 m)
-            const float ssw = Qsum - S2 / m;
+            const float ssw = Qsum - S2 * mf.x;
             float F = 0.f;
-            if (ssw > 0.f) F = (dev2 / ssw) * (((float)PPM_NG * (m - 1.0f)) / ((float)(PPM_NG - 1) * m));
+            if (ssw > 0.f) F = (dev2 / ssw) * mf.y;
             if (c == 0) F0 = CHI2 ? (float)x2 : F;
             if (!CHI2 && ssw > 0.f && (double)F > pr.fc[tpi]) reject = true;
             if constexpr (FEAT)
@@ -1008,6 +1011,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<MAPPING, NTC>)
 k_gather_update(GatherArgs a, Prob pr)
 {
     __shared__ BlockShared<NCH, NTC, MAPPING> bsh;
+    if (*a.err & 4) return;          // the grid's sort gave up: no usable grid
     const int64_t h0 = (int64_t)blockIdx.x * kThreads;
     gather_block<NCH, NTC, NORMALS, VCM, MAPPING, false, FEAT, CHI2>(a, pr, h0, a.nh, bsh);
 }

@@ -98,11 +98,14 @@ k_pack_keys(int64_t n, const float* __restrict__ pos, const float* __restrict__ 
 
 // One thread per sorted photon i in [0, n]: fills the buckets between the
 // previous photon's bucket and its own (exclusive/inclusive), so every
-// bucket in [0, T] is written exactly once.
+// bucket in [0, T] is written exactly once.  Nothing is written when the
+// sort's look-back gave up (*err bit 2): the keys are then no sorted
+// permutation and could point past the table.
 __global__ void __launch_bounds__(256)
 k_cell_start(const uint32_t* __restrict__ keys, int64_t n, uint32_t T,
-             uint32_t* __restrict__ cell_start)
+             uint32_t* __restrict__ cell_start, const int32_t* __restrict__ err)
 {
+    if (*err & 4) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     int64_t lo = 0, hi = -1;
@@ -126,15 +129,17 @@ k_cell_start(const uint32_t* __restrict__ keys, int64_t n, uint32_t T,
 }
 
 // records of packed photon vals[i] (stride 1 + REC1 + AUX float4s) into
-// the gather's separate sorted arrays
+// the gather's separate sorted arrays; nothing when the sort gave up (the
+// values are then no permutation of [0, n))
 template <bool REC1, bool AUX>
 __global__ void __launch_bounds__(256)
 k_permute(int64_t n, const uint32_t* __restrict__ vals, const float4* __restrict__ pack,
-          float4* __restrict__ rec0, float4* __restrict__ rec1, uint4* __restrict__ aux)
+          float4* __restrict__ rec0, float4* __restrict__ rec1, uint4* __restrict__ aux,
+          const int32_t* __restrict__ err)
 {
     constexpr int S = 1 + (REC1 ? 1 : 0) + (AUX ? 1 : 0);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || (*err & 4)) return;
     const float4* src = pack + (int64_t)vals[i] * S;
     rec0[i] = __ldg(src);
     if constexpr (REC1) rec1[i] = __ldg(src + 1);
@@ -231,15 +236,15 @@ int ppm_grid_build(ppm_ctx* c, const ppm_photons* ph)
             else launch_pack<1, false, false>(c, ph, nb);
         }
         PPM_LAUNCH_CHECK();
-        rc = ppm_radix_sort_pairs_lookback(&c->sort, n, c->tbits, c->err_dev, c->stream);
+        rc = ppm_radix_sort_pairs_lookback(&c->sort, n, c->tbits, c->err_dev, c->stream, c->prm.wait_limit);
         if (rc) return rc;
     }
-    rc = ppm_cell_start_launch(c->sort.keys, n, T, c->cell_start, c->stream);
+    rc = ppm_cell_start_launch(c->sort.keys, n, T, c->cell_start, c->err_dev, c->stream);
     if (rc) return rc;
     if (n > 0) {
         const bool rec1 = c->nch == 3 || vcm;
         rc = ppm_permute_launch(n, c->sort.vals, c->pack, c->rec0, rec1 ? c->rec1 : nullptr,
-                                aux ? c->aux : nullptr, c->stream);
+                                aux ? c->aux : nullptr, c->err_dev, c->stream);
         if (rc) return rc;
     }
     c->n_ph = n;
@@ -248,26 +253,26 @@ int ppm_grid_build(ppm_ctx* c, const ppm_photons* ph)
 }
 
 int ppm_cell_start_launch(const uint32_t* keys, int64_t n, uint32_t T, uint32_t* cell_start,
-                          cudaStream_t st)
+                          const int32_t* err, cudaStream_t st)
 {
-    k_cell_start<<<(unsigned)((n + 1 + 255) / 256), 256, 0, st>>>(keys, n, T, cell_start);
+    k_cell_start<<<(unsigned)((n + 1 + 255) / 256), 256, 0, st>>>(keys, n, T, cell_start, err);
     PPM_LAUNCH_CHECK();
     return PPM_OK;
 }
 
 int ppm_permute_launch(int64_t n, const uint32_t* vals, const float4* pack, float4* rec0, float4* rec1,
-                       uint4* aux, cudaStream_t st)
+                       uint4* aux, const int32_t* err, cudaStream_t st)
 {
     if (n <= 0) return PPM_OK;
     const unsigned nb = (unsigned)((n + 255) / 256);
     if (rec1 && aux)
-        k_permute<true, true><<<nb, 256, 0, st>>>(n, vals, pack, rec0, rec1, aux);
+        k_permute<true, true><<<nb, 256, 0, st>>>(n, vals, pack, rec0, rec1, aux, err);
     else if (rec1)
-        k_permute<true, false><<<nb, 256, 0, st>>>(n, vals, pack, rec0, rec1, aux);
+        k_permute<true, false><<<nb, 256, 0, st>>>(n, vals, pack, rec0, rec1, aux, err);
     else if (aux)
-        k_permute<false, true><<<nb, 256, 0, st>>>(n, vals, pack, rec0, rec1, aux);
+        k_permute<false, true><<<nb, 256, 0, st>>>(n, vals, pack, rec0, rec1, aux, err);
     else
-        k_permute<false, false><<<nb, 256, 0, st>>>(n, vals, pack, rec0, rec1, aux);
+        k_permute<false, false><<<nb, 256, 0, st>>>(n, vals, pack, rec0, rec1, aux, err);
     PPM_LAUNCH_CHECK();
     return PPM_OK;
 }

@@ -28,6 +28,14 @@
 
 void ppm_note_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 
+// The return code that a call reporting the device error flags gives:
+// bit 2 (a bounded device wait gave up) before bit 0 (a gather skipped
+// cells); bit 1 (a window clamped to the F_c table) is only reported.
+inline int ppm_flags_status(int32_t flags)
+{
+    return (flags & 4) ? PPM_ETIMEOUT : ((flags & 1) ? PPM_EINCOMPLETE : PPM_OK);
+}
+
 // ---------------------------------------------------------------------------
 // Grid: a uniform grid of cell edge h, hashed into T = 2^tbits buckets.
 // Cells are grouped in blocks of B^3 (B = 2^lb); the low 3*lb bits of a
@@ -108,9 +116,12 @@ struct SortScratch {
 int ppm_radix_sort_pairs(SortScratch* s, int64_t n, int bits, cudaStream_t st);
 // The same sort in one kernel per pass (decoupled look-back between the
 // blocks of a pass; the counts of every pass first).  A look-back wait that
-// gives up (it should never) sets bit 2 of *err (device).  Launches 2 +
+// gives up after spin_limit polls (0: the default 2^22; it should never
+// happen) sets bit 2 of *err (device); every write stays inside [0, n), but
+// the keys and values are then no permutation of the input.  Launches 2 +
 // ceil(bits / 8) kernels.
-int ppm_radix_sort_pairs_lookback(SortScratch* s, int64_t n, int bits, int32_t* err, cudaStream_t st);
+int ppm_radix_sort_pairs_lookback(SortScratch* s, int64_t n, int bits, int32_t* err, cudaStream_t st,
+                                  int spin_limit = 0);
 int ppm_sort_scratch_reserve(SortScratch* s, int64_t n);
 void ppm_sort_scratch_free(SortScratch* s);
 
@@ -125,6 +136,8 @@ int ppm_fcrit_fill(double* table, int t_from, int t_to, double J, double alpha,
                    cudaStream_t st);
 // every entry t_from .. t_to = the (1 - alpha) quantile of chi^2(k)
 int ppm_chi2_fill(double* table, int t_from, int t_to, double k, double alpha, cudaStream_t st);
+// mtab[t] = (1/m, 12 (m-1) / (11 m)) with m = t J samples per group, from FP64
+int ppm_window_m_fill(float2* mtab, int t_from, int t_to, double J, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Context
@@ -172,8 +185,10 @@ struct ppm_ctx {
     // built for; the update writes rmax[cur ^ 1]
     float* rmax = nullptr;        // 2 floats
     int rmax_cur = 0;
-    // F_c table, indexed by window length t' (1-based)
+    // F_c table, indexed by window length t' (1-based), and the F statistic's
+    // factors of m = t' J for the same t' (ppm_window_m_fill)
     double* fc = nullptr;
+    float2* fm = nullptr;
     int fc_cap = 0;
     int fc_upto = 0;
     // counters: [0] pairs, [1] candidates, [2] rejects, [3] pairs_total
@@ -211,12 +226,14 @@ struct ppm_ctx {
 int ppm_grid_build(ppm_ctx* c, const ppm_photons* ph);
 // bucket-table size for n photons and hash blocks of 2^lb cells per axis
 int ppm_table_bits(int64_t n, int lb);
-// cell_start[b] = first sorted photon with bucket >= b, b in [0, T]
+// cell_start[b] = first sorted photon with bucket >= b, b in [0, T]; no
+// writes when *err (device) has bit 2 (the sort's look-back gave up)
 int ppm_cell_start_launch(const uint32_t* keys, int64_t n, uint32_t T, uint32_t* cell_start,
-                          cudaStream_t st);
-// packed records gathered into sorted order (rec1 / aux when non-NULL)
+                          const int32_t* err, cudaStream_t st);
+// packed records gathered into sorted order (rec1 / aux when non-NULL);
+// nothing when *err has bit 2
 int ppm_permute_launch(int64_t n, const uint32_t* vals, const float4* pack, float4* rec0, float4* rec1,
-                       uint4* aux, cudaStream_t st);
+                       uint4* aux, const int32_t* err, cudaStream_t st);
 // ppm_api.cu: hit points -> Hilbert-sorted internal layout (synchronizes st)
 int ppm_prepare_hitpoints(const ppm_hitpoints* hp, bool with_rho, uint32_t* orig, float4* pos,
                           float4* u, float4* v, cudaStream_t st);

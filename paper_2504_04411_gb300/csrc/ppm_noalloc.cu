@@ -2,23 +2,23 @@
 // ppm_sort_pairs (in its three-kernel-per-pass form, same results) with its
 // scratch in a fixed device array instead of memory allocated per call.
 //
-// For callers that must not allocate device memory while they run: code
-// being recorded into a CUDA graph (stream capture forbids cudaMalloc),
-// real-time loops that cannot afford an allocator call or its implicit
-// synchronization, and hosts whose device memory is entirely owned by
-// another allocator.  The scratch (both ping-pong arrays, the per-tile
-// digit histograms and the scan partials for up to PPM_NOALLOC_MAX_PAIRS
-// pairs, ~8.6 MB) is a file-scope __device__ array: every GPU that loads
-// this library holds it until the process exits.
+// For callers that cannot call cudaMalloc while they run: real-time loops
+// that cannot pay for an allocator call or the synchronization it may
+// bring, and hosts whose device memory is entirely owned by another
+// allocator.  The scratch (both ping-pong arrays, the per-tile digit
+// histograms and the scan partials for up to PPM_NOALLOC_MAX_PAIRS = n
+// pairs: 2n + n/8 + 34 words, 8.9 MB) is a file-scope __device__ array:
+// every GPU that loads this library holds it until the process exits.
 //
 // In host code the array's name only stands for the symbol; its device
 // address is obtained once per device with cudaGetSymbolAddress while that
-// device is current (the first call on a device does this set-up, so make
-// that first call before any stream capture).  All calls share the array:
-// calls whose work overlaps on the GPU (different streams, or different
-// host threads on one device) race on it.  Every word of the scratch that a
-// call reads is written earlier in the same call, so nothing needs clearing
-// between calls.
+// device is current (the first call on a device does this set-up).  The
+// address is cached for the life of the process, so cudaDeviceReset after
+// the first call is not supported (the cached address would be stale).
+// All calls share the array: calls whose work overlaps on the GPU
+// (different streams, or different host threads on one device) race on
+// it.  Every word of the scratch that a call reads is written earlier in
+// the same call, so nothing needs clearing between calls.
 #include <mutex>
 
 #include "ppm_internal.cuh"

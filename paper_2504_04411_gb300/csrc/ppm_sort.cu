@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kSortThreads)
 k_radix_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                  uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
                  uint32_t mask, const uint32_t* __restrict__ goff, unsigned long long* status,
-                 int32_t* err)
+                 int32_t* err, int spin_limit)
 {
     __shared__ uint32_t s_cnt[kWarps][256];
     __shared__ uint32_t s_base[256];
@@ -229,7 +229,7 @@ k_radix_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ 
                 const unsigned long long x = ld_relaxed_u64(word + (int64_t)q * 256 + dg);
                 const unsigned long long f = x & ~kCountMask;
                 if (f == 0ull) {
-                    if (++spins > kSpinLimit) { atomicOr(err, 4); break; }
+                    if (++spins > spin_limit) { atomicOr(err, 4); break; }
                     __nanosleep(32);
                     continue;
                 }
@@ -449,8 +449,10 @@ int ppm_radix_sort_pairs(SortScratch* s, int64_t n, int bits, cudaStream_t st)
     return PPM_OK;
 }
 
-int ppm_radix_sort_pairs_lookback(SortScratch* s, int64_t n, int bits, int32_t* err, cudaStream_t st)
+int ppm_radix_sort_pairs_lookback(SortScratch* s, int64_t n, int bits, int32_t* err, cudaStream_t st,
+                                  int spin_limit)
 {
+    if (spin_limit <= 0) spin_limit = kSpinLimit;
     if (n <= 1 || bits <= 0) return PPM_OK;
     if (n > 0xFFFFFFFFll || bits > 32 || n > s->cap || !s->status || !s->digit || !err) return PPM_EINVAL;
     const int ntiles = (int)((n + kSweepTile - 1) / kSweepTile);
@@ -468,7 +470,8 @@ int ppm_radix_sort_pairs_lookback(SortScratch* s, int64_t n, int bits, int32_t* 
         const uint32_t mask = (1u << nb) - 1u;
         PPM_CUDA(cudaMemsetAsync(s->status, 0, (size_t)(kStatusHead + 256ll * ntiles) * sizeof(unsigned long long), st));
         k_radix_onesweep<<<ntiles, kSortThreads, 0, st>>>(s->keys, s->vals, s->keys_alt, s->vals_alt, n, shift,
-                                                         mask, s->digit + p * 256, s->status, err);
+                                                         mask, s->digit + p * 256, s->status, err,
+                                                         spin_limit);
         PPM_LAUNCH_CHECK();
         uint32_t* t;
         t = s->keys; s->keys = s->keys_alt; s->keys_alt = t;

@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libppm.so")
 
 PPM_OK, PPM_EINVAL, PPM_ENOMEM, PPM_ECUDA, PPM_ETIMEOUT, PPM_ESTATE = 0, -1, -2, -3, -4, -5
+PPM_EINCOMPLETE = -6
 PPM_NGROUPS = 12
 
 c_p = ctypes.c_void_p
@@ -39,7 +40,7 @@ class ppm_params(ctypes.Structure):
                 ("channels", ctypes.c_int32), ("rgb_test", ctypes.c_int32),
                 ("vcm", ctypes.c_int32), ("n_vm", ctypes.c_float),
                 ("mapping", ctypes.c_int32), ("tile", ctypes.c_int32), ("test", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("wait_limit", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class ppm_iter_stats(ctypes.Structure):

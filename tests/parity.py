@@ -7,13 +7,18 @@ from dataclasses import dataclass, field
 import numpy as np
 
 # Reject decisions are compared bit for bit wherever the oracle's FP64 F is
-# farther than BAND * F_c from F_c.  Inside the band the GPU's F (FP32 window
-# sums, FP32 F) may fall on the other side: both decisions are correct
-# readings of the same data, and that hit point's later trajectory is
-# excluded from the comparison (counted as "diverged").
-BAND = 1e-3
-S_RTOL = 2e-5      # FP32 window sums against FP64
+# farther than BAND * F_c from F_c (the scope table's 1e-4).  Inside the
+# band the GPU's F (FP32 window sums, FP32 F) may fall on the other side:
+# both decisions are correct readings of the same data, and that hit
+# point's later trajectory is excluded from the comparison (counted as
+# "diverged").  The measured F error (<= 3e-6 relative) leaves a 30x margin.
+BAND = 1e-4
+S_RTOL = 2e-5      # FP32 window sums S_g, Q_g against FP64, per group
+F_RTOL = 1e-5      # the F statistic of the last test, per hit point
 L_RTOL = 1e-5      # radiance / estimate against FP64
+# absolute floors, relative to the largest value of the compared array:
+# only values that are zero (or within FP32 underflow of it) use them
+FLOOR = 1e-9
 
 
 @dataclass
@@ -50,10 +55,35 @@ def run_gpu(hp, batches, r0, alpha=0.75, params=None, J=None, hps=None):
     return states, stats, L
 
 
-def compare(states, stats, L, ref, iters, ch_test=0, band=BAND, check_pairs=True) -> Report:
+def _close(got, want, rtol, what, it):
+    """Element-wise |got - want| <= rtol |want| + FLOOR max|want|; returns
+    the largest relative error over the nonzero entries."""
+    got = np.asarray(got, np.float64)
+    want = np.asarray(want, np.float64)
+    if want.size == 0:
+        return 0.0
+    floor = FLOOR * float(np.abs(want).max())
+    err = np.abs(got - want)
+    bad = err > rtol * np.abs(want) + floor
+    assert not bad.any(), (f"{what} differs at iteration {it + 1}: {int(bad.sum())} entries, "
+                           f"e.g. got {got[bad][:4]} want {want[bad][:4]}")
+    nz = np.abs(want) > floor
+    return float((err[nz] / np.abs(want[nz])).max()) if nz.any() else 0.0
+
+
+def compare(states, stats, L, ref, iters, band=BAND, check_pairs=True) -> Report:
+    """Every iteration's GPU state against the oracle's, element by element:
+    radii, window lengths, per-group counts (exact); decisions (exact outside
+    the band); per-group window sums S and Q of every tested channel, F of
+    the last test, the iteration's estimate term (tau difference) of every
+    hit point (within the tolerances above); the final radiance."""
     rep = Report(iters=iters, n=states[0]["r"].shape[0])
     n = rep.n
     diverged = np.zeros(n, bool)
+    ntc = states[0]["S"].shape[1]
+    Sc = ref.Sc if ref.Sc is not None else ref.S[:, :, None, :]
+    Qc = ref.Qc if ref.Qc is not None else ref.Q[:, :, None, :]
+    assert Sc.shape[2] == ntc, (Sc.shape, ntc)
     for it in range(iters):
         g = states[it]
         rej_o = ref.reject[it]
@@ -77,29 +107,28 @@ def compare(states, stats, L, ref, iters, ch_test=0, band=BAND, check_pairs=True
         assert stats[it]["flags"] == 0
         same = alive & ~flip
         assert np.array_equal(g["r"][same], ref.r[it + 1][same])
+        assert np.array_equal(g["t"][same & ~rej_o], (states[it - 1]["t"][same & ~rej_o] + 1) if it > 0
+                              else np.ones(int((same & ~rej_o).sum()), np.int32))
         keep = same & ~rej_o
         assert np.array_equal(g["counts"][keep], ref.counts[it][keep]), f"counts differ at iteration {it + 1}"
         assert np.all(g["counts"][same & rej_o] == 0)
-        So = ref.S[it][keep]
-        Sg = g["S"][keep][:, ch_test, :].astype(np.float64)
-        scale = np.abs(So).sum(1, keepdims=True) + 1e-30
-        relS = np.abs(Sg - So) / scale
-        rep.max_rel_S = max(rep.max_rel_S, float(relS.max()) if relS.size else 0.0)
-        assert rep.max_rel_S <= S_RTOL, rep.max_rel_S
-        okF = keep & (Fo > 0)
-        if okF.any():
-            relF = np.abs(g["F"][okF].astype(np.float64) - Fo[okF]) / Fo[okF]
-            rep.max_rel_F = max(rep.max_rel_F, float(relF.max()))
+        assert np.all(g["S"][same & rej_o] == 0) and np.all(g["Q"][same & rej_o] == 0)
+        # window sums of every tested channel, per group
+        rep.max_rel_S = max(rep.max_rel_S, _close(g["S"][keep], Sc[it][keep], S_RTOL, "S", it))
+        rep.max_rel_S = max(rep.max_rel_S, _close(g["Q"][keep], Qc[it][keep], S_RTOL, "Q", it))
+        # F of this iteration's test (rejected hit points included)
+        rep.max_rel_F = max(rep.max_rel_F, _close(g["F"][same], Fo[same], F_RTOL, "F", it))
+        # this iteration's estimate term of every hit point (rejected included)
+        if ref.est is not None:
+            prev = states[it - 1]["tau"] if it > 0 else np.zeros_like(g["tau"])
+            dtau = (g["tau"] - prev).reshape(ref.est[it].shape)
+            rep.max_rel_L = max(rep.max_rel_L, _close(dtau[same], ref.est[it][same], L_RTOL, "estimate term", it))
         diverged |= flip
     rep.diverged = int(diverged.sum())
     alive = ~diverged
     Lo = ref.tau / iters
     Lg = L.reshape(Lo.shape).astype(np.float64)
-    scale = np.abs(Lo).max() + 1e-30
-    relL = np.abs(Lg[alive] - Lo[alive]) / np.maximum(np.abs(Lo[alive]), 1e-3 * scale)
-    rep.max_rel_L = float(relL.max()) if relL.size else 0.0
-    assert rep.max_rel_L <= L_RTOL, rep.max_rel_L
+    rep.max_rel_L = max(rep.max_rel_L, _close(Lg[alive], Lo[alive], L_RTOL, "radiance", iters - 1))
     tau_g = states[-1]["tau"].reshape(ref.tau.shape)
-    relT = np.abs(tau_g[alive] - ref.tau[alive]) / np.maximum(np.abs(ref.tau[alive]), 1e-3 * np.abs(ref.tau).max() + 1e-300)
-    assert relT.max() <= L_RTOL if relT.size else True
+    _close(tau_g[alive], ref.tau[alive], L_RTOL, "tau", iters - 1)
     return rep

@@ -37,8 +37,11 @@ def test_default_params_and_strerror_without_gpu():
     p = ppm.ppm_default_params()
     assert p.k == pytest.approx(0.7) and p.alpha_f == pytest.approx(0.01)
     assert p.rmin_ratio == pytest.approx(1e-3) and p.cell_factor == 1.0
-    assert p.test == 0 and p.mapping == 0 and p.tile == 0 and list(p.reserved) == [0] * 4
+    assert p.test == 0 and p.mapping == 0 and p.tile == 0 and p.wait_limit == 0
+    assert list(p.reserved) == [0] * 3
     assert ppm.ppm_strerror(ppm.PPM_ESTATE) == "call out of order"
+    assert ppm.ppm_strerror(ppm.PPM_ETIMEOUT) == "bounded device wait timed out"
+    assert ppm.ppm_strerror(ppm.PPM_EINCOMPLETE).startswith("a gather skipped cells")
 
 
 def test_struct_layouts_match_header():

@@ -141,3 +141,35 @@ def test_batch_rejects_bad_iterations():
     b.step(good)
     assert b.stats()[0].iter == 1
     b.close()
+
+
+def test_batch_windows_beyond_the_initial_critical_value_table():
+    """Windows longer than the 1024 window lengths tabulated at create: the
+    tables grow (the graph is captured again), no window is clamped to the
+    table (flags bit 1 stays clear) and the F of windows past 1024 matches
+    the oracle (within the FP32 drift of 1030-iteration window sums)."""
+    import torch
+    from paper_2504_04411_gb300 import ppm
+    iters = 1030
+    scenes = [synth.PlaneScene(nside=6, J=600, r0=0.12, step=False, seed=synth.SEED_BASE + 500 + i)
+              for i in range(2)]
+    hps = [s.hitpoints("cuda") for s in scenes]
+    phs = [[s.photons(i, "cuda") for s in scenes] for i in range(1, iters + 1)]
+    b = ppm.Batch(hps, [s.r0 for s in scenes], [s.J for s in scenes], params=_params(alpha_f=1e-9))
+    for it in range(iters):
+        b.step(phs[it])
+        if it == 2:
+            assert ppm.ppm_batch_graph_ready(b.b)
+    stats = b.stats()
+    states = [{k: v.cpu().numpy() for k, v in b.state(p).items()} for p in range(len(scenes))]
+    b.close()
+    torch.cuda.synchronize()
+    for p, sc in enumerate(scenes):
+        assert stats[p].flags == 0 and stats[p].iter == iters
+        ref = O.run(hps[p].numpy(), synth.stack_numpy([ph[p] for ph in phs]),
+                    sc.r0, iters, alpha_f=1e-9)
+        st = states[p]
+        assert np.array_equal(st["t"], ref.t) and np.array_equal(st["r"], ref.r[-1])
+        assert ref.t.max() > 1024                     # windows past the initial table
+        long = ref.t > 1024
+        assert np.allclose(st["F"][long], ref.F[-1][long], rtol=1e-3, atol=1e-6)

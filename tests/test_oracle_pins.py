@@ -314,6 +314,51 @@ def _independent_in_disk(hp, ph, r):
     return ((d2 <= (r * (1 - 1e-5)) ** 2).sum(1), (d2 <= (r * (1 + 1e-5)) ** 2).sum(1))
 
 
+def _rec709_luminance_row():
+    """Y row of the RGB -> XYZ matrix of ITU-R BT.709: the primaries'
+    chromaticities (R 0.64/0.33, G 0.30/0.60, B 0.15/0.06) scaled so that
+    R = G = B = 1 gives the D65 white point (x 0.3127, y 0.3290) with Y = 1."""
+    prim = np.array([[0.64, 0.33], [0.30, 0.60], [0.15, 0.06]])
+    xyz = np.array([[x / y, 1.0, (1 - x - y) / y] for x, y in prim]).T   # columns: R, G, B
+    wx, wy = 0.3127, 0.3290
+    white = np.array([wx / wy, 1.0, (1 - wx - wy) / wy])
+    scale = np.linalg.solve(xyz, white)
+    return xyz[1] * scale
+
+
+def test_luminance_weights_are_rec709():
+    # the weights follow from the BT.709 primaries and white point (to the
+    # four decimals the standard quotes), not from a retyped table
+    y = _rec709_luminance_row()
+    assert y.sum() == pytest.approx(1.0, abs=1e-12)
+    for rgb, want in (((1, 0, 0), y[0]), ((0, 1, 0), y[1]), ((0, 0, 1), y[2])):
+        assert O.lum(*rgb) == pytest.approx(want, abs=5e-5)
+    assert O.lum(1, 1, 1) == pytest.approx(1.0, abs=1e-12)
+    # linear: scaling and adding fluxes
+    assert O.lum(0.3, 2.0, 0.7) == pytest.approx(0.3 * O.lum(1, 0, 0) + 2 * O.lum(0, 1, 0) + 0.7 * O.lum(0, 0, 1),
+                                                 rel=1e-14)
+
+
+def test_run_tests_the_luminance_of_rgb_flux():
+    # one hit point, one photon inside its disk: the tested value in the
+    # window is the photon's luminance; the estimate keeps all three channels
+    hp = {"pos": np.array([[0.5, 0.5, 0.0]], np.float32), "u": np.array([[1, 0, 0]], np.float32),
+          "v": np.array([[0, 1, 0]], np.float32)}
+    rgb = np.array([0.25, 0.5, 2.0], np.float32)
+    ph = {"pos": np.array([[[0.505, 0.5, 0.0], [0.9, 0.9, 0.0]]], np.float32),
+          "flux": np.array([[rgb, [1, 1, 1]]], np.float32)}
+    res = O.run(hp, ph, 0.02, 1, alpha_f=1e-12)
+    y = _rec709_luminance_row()
+    assert res.S[0, 0].sum() == pytest.approx(float(y @ rgb.astype(np.float64)), rel=1e-4)
+    assert res.S[0, 0].sum() == pytest.approx(O.lum(*rgb.astype(np.float64)), rel=1e-15)
+    assert res.Q[0, 0].sum() == pytest.approx(O.lum(*rgb.astype(np.float64)) ** 2, rel=1e-15)
+    area = math.pi * float(np.float32(0.02)) ** 2
+    assert np.allclose(res.tau[0], rgb.astype(np.float64) / area, rtol=1e-12)
+    # per-channel mode: three windows, one per channel
+    res3 = O.run(hp, ph, 0.02, 1, alpha_f=1e-12, rgb_test=True)
+    assert np.allclose(res3.Sc[0, 0].sum(axis=1), rgb, rtol=1e-12)
+
+
 def test_run_counts_match_geometry():
     sc = synth.PlaneScene(nside=16, J=5000, r0=0.06, step=True)
     hp = sc.hitpoints().numpy()

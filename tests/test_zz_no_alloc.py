@@ -1,5 +1,5 @@
-"""ppm_sort_pairs_noalloc, the sort for callers that cannot allocate device
-memory (graph capture, real-time loops, foreign allocators): through the C
+"""ppm_sort_pairs_noalloc, the sort for callers that cannot call cudaMalloc
+(real-time loops, device memory owned by another allocator): through the C
 ABI its output must equal ppm_sort_pairs' exactly, on two calls in a row
 (the fixed scratch array keeps the previous call's contents), and sizes
 beyond its fixed capacity must be refused.  Runs last so a failure here
