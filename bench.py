@@ -5,7 +5,13 @@ photon grid (cell key, stable radix sort, cell ranges, permute) and gather /
 F-test / update every hit point.
 
 Workloads (--config):
-  frame    (default) 1920x1080 hit points on the three faces z=0, y=0, x=0 of
+  vcm      (default) the VCM+ merge workload at 4K: 3840x2160 hit points on
+           the three faces of the unit box, 16,000,000 light vertices per
+           iteration with RGB flux (tinted caustic lobes), log-normal MIS pdf
+           ratios and cosine-distributed incoming directions, r0 = 0.0026
+           (0.3% of the bounding radius), k = 0.9, luminance F-test, every
+           pair weighted by the merge weight -- the largest configuration;
+  frame    1920x1080 hit points on the three faces z=0, y=0, x=0 of
            the unit box, 2,000,000 photons per iteration (uniform density +
            2 anisotropic Gaussian caustic lobes + 2 step-edge shadows),
            r0 = 0.01, 64 iterations in total (warm-up + timed);
@@ -49,12 +55,21 @@ GATHER_BYTES_PER_PHOTON_VCM = 16 + 16 + 16
 GATHER_BYTES_PER_HIT_VCM = 48 + 4 + 4 + 24 + 144 + (4 + 4 + 24 + 4 + 144)
 # static record read; r, t, tau and the window (12 x count, S, Q) read;
 # r, t, tau, F and the window written
-# algorithmic FP32/INT operations of the canonical per-pair sequence
-OPS_PER_CANDIDATE = 7     # 3 sub, 1 mul + 2 fma (d^2), 1 compare
-OPS_PER_PAIR = 28         # normal dp4a+cmp 2, map 6, rho^2 2, ring 2, sector 9, group 1, accumulate 4, flux 2
-# + merge weight (cosine dp4a, scale, 2 fma/add, R_VC/eta, reciprocal: 8),
-# weighted psi 1, weighted RGB flux 3, compensated RGB sums 12
-OPS_PER_PAIR_VCM = OPS_PER_PAIR + 8 + 1 + 3 + 12
+# algorithmic operations per candidate photon and per in-disk pair.  The
+# scope table's model (the headline roofline): 8 per candidate, 15 per pair,
+# and ~1 reciprocal + 8 FMA more per pair for the VCM+ merge weight.
+OPS_PER_CANDIDATE = 8
+OPS_PER_PAIR = 15
+OPS_PER_PAIR_VCM = OPS_PER_PAIR + 9
+# the canonical FP32/INT sequence counted instruction by instruction
+# (reported beside it): 3 sub, 1 mul + 2 fma (d^2), 1 compare per candidate;
+# normal dp4a+cmp 2, map 6, rho^2 2, ring 2, sector 9, group 1, accumulate
+# 4, flux 2 per pair; VCM+ adds the merge weight (cosine dp4a, scale, 2
+# fma/add, R_VC/eta, reciprocal: 8), weighted psi 1, weighted RGB flux 3 and
+# the compensated RGB sums 12
+OPS_PER_CANDIDATE_DETAILED = 7
+OPS_PER_PAIR_DETAILED = 28
+OPS_PER_PAIR_VCM_DETAILED = OPS_PER_PAIR_DETAILED + 8 + 1 + 3 + 12
 
 
 def _peaks():
@@ -144,9 +159,11 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- oracle --
 def oracle_sample(scene, batches_np, hp_np, n_hits, seed=0, **kw):
-    """Run the CPU oracle (as it stands) over one iteration for a random
-    subset of hit points; returns (pairs, seconds).  kw: method options of
-    oracle.run (vcm, k)."""
+    """Run the CPU oracle (as it stands) in its grid form -- photons sorted
+    by cell, each disk's cells scanned, FP64 statistics, OpenMP over hit
+    points -- over one iteration for a random subset of hit points; returns
+    (pairs, seconds, seconds of the grid build).  kw: method options of
+    oracle.run (vcm, k, test)."""
     import numpy as np
 
     from oracle import oracle as O
@@ -154,7 +171,7 @@ def oracle_sample(scene, batches_np, hp_np, n_hits, seed=0, **kw):
     idx = np.sort(rng.choice(hp_np["pos"].shape[0], n_hits, replace=False))
     sub = {k: v[idx] for k, v in hp_np.items()}
     t0 = time.perf_counter()
-    res = O.run(sub, batches_np, scene.r0, 1, outputs=True, **kw)
+    res = O.run(sub, batches_np, scene.r0, 1, outputs=True, grid=True, **kw)
     dt = time.perf_counter() - t0
     return int(res.pairs.sum()), dt
 
@@ -162,14 +179,18 @@ def oracle_sample(scene, batches_np, hp_np, n_hits, seed=0, **kw):
 def cpu_baseline(scene, hp_np, ph_np, budget_s=12.0, **kw):
     threads = os.cpu_count() or 1
     os.environ.setdefault("OMP_NUM_THREADS", str(threads))
-    probe = 128
+    probe = 4096
+    _, dt0 = oracle_sample(scene, ph_np, hp_np, 16, seed=1, **kw)          # ~ the grid build alone
     _, dt = oracle_sample(scene, ph_np, hp_np, probe, seed=1, **kw)
-    n = int(min(hp_np["pos"].shape[0], max(probe, probe * budget_s / max(dt, 1e-3))))
+    per_hit = max(dt - dt0, 1e-6) / probe
+    n = int(min(hp_np["pos"].shape[0], max(probe, (budget_s - dt0) / per_hit)))
     pairs, dt = oracle_sample(scene, ph_np, hp_np, n, seed=2, **kw)
     return {"value": pairs / dt, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", threads)),
             "kind": "oracle",
             "sample": f"{n} random hit points of the workload x 1 iteration of {ph_np['pos'].shape[1]} "
-                      f"photons, brute force all pairs, FP64 statistics, {dt:.1f} s"}
+                      f"photons; the oracle's grid form (photons sorted by cell, each disk's cells "
+                      f"scanned, the same FP32 classification, FP64 statistics); {dt:.1f} s including "
+                      f"one grid build of all photons (~{dt0:.1f} s, single thread)"}
 
 
 # ------------------------------------------------------------------ main ---
@@ -179,8 +200,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="frame",
-                    choices=["frame", "tiny", "batched", "learned", "vcm", "cppm", "sweep"])
+    ap.add_argument("--config", default="vcm",
+                    choices=["frame", "tiny", "batched", "learned", "learned_frame", "vcm", "cppm", "sweep"])
     ap.add_argument("--mapping", type=int, default=None, help="skip the autotuner: traversal")
     ap.add_argument("--cell-factor", type=float, default=None, help="skip the autotuner: cell factor")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -188,7 +209,8 @@ def parse():
     ap.add_argument("--no-flush", action="store_true")
     a = ap.parse_args()
     if a.steps is None:
-        a.steps = 16 if a.config in ("batched", "vcm") else (64 if a.config in ("learned", "cppm", "sweep")
+        a.steps = 16 if a.config in ("batched", "vcm") else (64 if a.config in ("learned", "learned_frame", "cppm",
+                                                                                 "sweep")
                                                              else 64 - a.warmup)
     return a
 
@@ -224,6 +246,8 @@ def roofline(g_ms, photons, hits, candidates, pairs, sm_count, kernel, vcm=False
     hbm_achieved = bytes_launch / g_s / 1e9
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     ops_launch = candidates * OPS_PER_CANDIDATE + pairs * (OPS_PER_PAIR_VCM if vcm else OPS_PER_PAIR)
+    ops_detailed = candidates * OPS_PER_CANDIDATE_DETAILED + pairs * (OPS_PER_PAIR_VCM_DETAILED if vcm
+                                                                      else OPS_PER_PAIR_DETAILED)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     alu_peak = sm_count * 128 * sm_mhz * 1e6 / 1e12
     alu_achieved = ops_launch / g_s / 1e12
@@ -232,7 +256,13 @@ def roofline(g_ms, photons, hits, candidates, pairs, sm_count, kernel, vcm=False
            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"}
     alu = {"bound": "alu", "achieved": round(alu_achieved, 3), "peak": round(alu_peak, 2), "unit": "Tops/s",
            "frac": round(alu_achieved / alu_peak, 4), "algorithmic_ops": ops_launch, "kernel": kernel,
-           "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (recipe unit counts, max clock)"}
+           "op_model": f"{OPS_PER_CANDIDATE} per candidate + {OPS_PER_PAIR_VCM if vcm else OPS_PER_PAIR} "
+                       f"per in-disk pair (scope-table model)",
+           "frac_detailed_ops": round(ops_detailed / g_s / 1e12 / alu_peak, 4),
+           "detailed_op_model": f"{OPS_PER_CANDIDATE_DETAILED} per candidate + "
+                                f"{OPS_PER_PAIR_VCM_DETAILED if vcm else OPS_PER_PAIR_DETAILED} per pair",
+           "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (recipe unit counts, max clock; "
+                          f"derived, not measured)"}
     return (alu, hbm) if alu["frac"] >= hbm["frac"] else (hbm, alu)
 
 
@@ -259,7 +289,7 @@ def main():
     __graft_entry__.build()
     if args.config == "batched":
         line = run_batched(args, rank, world, local, dist)
-    elif args.config == "learned":
+    elif args.config in ("learned", "learned_frame"):
         line = run_learned(args, rank, world, local, dist)
     elif args.config == "cppm":
         line = run_cppm(args, rank, world, local, dist)
@@ -517,28 +547,50 @@ def run_batched(args, rank, world, local, dist):
 
 
 def run_learned(args, rank, world, local, dist):
-    """Learned radius proposer vs the plain method on the tiny configuration
-    at equal radiance MSE: the network is trained (own kernels) on 200 plain
-    iterations of one seed, both methods then run on a fresh seed; the
-    metric is the learned run's pair-test rate, with the iterations and
-    device time each needs to reach the plain method's final MSE."""
+    """Learned radius proposer vs the plain method at equal radiance MSE.
+    --config learned: the tiny configuration; the network is trained (own
+    kernels) on 200 plain iterations of one seed, both methods then run on a
+    fresh seed.  --config learned_frame: the frame-sized box scene (2M hit
+    points, 2M photons per iteration, r0 = 0.01); the network is trained on
+    100 plain iterations of a box scene of another seed with the same photon
+    density (300k hit points, so the training set stays ~30M samples), then
+    both methods run 64 iterations of the frame workload, MSE against the
+    scene's closed-form irradiance.  The metric is the learned run's
+    pair-test rate, with the iterations and device time each needs to reach
+    the plain method's final MSE."""
     import torch
 
     from paper_2504_04411_gb300 import learned, ppm, synth
     N = args.steps if args.steps else 64
-    train_sc = synth.PlaneScene(nside=64, J=100_000, r0=0.02, step=True, seed=synth.SEED_BASE + 500 + 1000 * rank)
+    frame = args.config == "learned_frame"
+    if frame:
+        train_sc = synth.BoxScene(nh=300_000, seed=synth.SEED_BASE + 510 + 1000 * rank)
+        train_iters = 100
+    else:
+        train_sc = synth.PlaneScene(nside=64, J=100_000, r0=0.02, step=True,
+                                    seed=synth.SEED_BASE + 500 + 1000 * rank)
+        train_iters = 200
     t0 = time.perf_counter()
-    tr = learned.run(train_sc, 200)
+    tr = learned.run(train_sc, train_iters)
     X, Y, M = learned.dataset(tr)
+    del tr
     blob, _, losses = learned.train(X, Y, M, epochs=20)
     train_s = time.perf_counter() - t0
-    test_sc = synth.PlaneScene(nside=64, J=100_000, r0=0.02, step=True, seed=synth.SEED_BASE + 600 + 1000 * rank)
-    hp = test_sc.hitpoints("cuda")
-    ref = (hp.pos[:, 0] < 0.5).float()
+    if frame:
+        test_sc, desc = make_scene("frame", rank)
+        hp = test_sc.hitpoints("cuda")
+        ref = test_sc.irradiance(hp).to("cuda", torch.float32)
+        params = _params(args)
+    else:
+        test_sc = synth.PlaneScene(nside=64, J=100_000, r0=0.02, step=True,
+                                   seed=synth.SEED_BASE + 600 + 1000 * rank)
+        hp = test_sc.hitpoints("cuda")
+        ref = (hp.pos[:, 0] < 0.5).float()
+        params = None
     batches = [test_sc.photons(i, "cuda") for i in range(1, N + 1)]
 
     def timed(blob_):
-        est = ppm.Estimator(hp, test_sc.r0, 0.75)
+        est = ppm.Estimator(hp, test_sc.r0, 0.75, params)
         if blob_ is not None:
             ppm.ppm_set_mlp(est.ctx, blob_, 0.5, 0.1)
         ms, mse, pairs = [], [], 0
@@ -564,16 +616,24 @@ def run_learned(args, rank, world, local, dist):
     return {"metric": METRIC, "value": lpairs / (sum(lms) / 1e3), "unit": UNIT, "n_gpus": world,
             "steps": N, "warmup": 0, "ms_per_step": sum(lms) / N, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (BF16 network weights)", "data": "synthetic",
-            "config": {"workload": "learned radius: tiny config (64x64 hit points, 100k photons/iter, "
-                                   "step edge, r0=0.02), MLP 12-64-64-2 trained on 200 plain iterations",
-                       "hit_points": 4096, "photons_per_iter": 100_000, "l2": "not flushed (small)",
-                       "parallelism": "single GPU"},
+            "config": ({"workload": "learned radius, frame-sized: " + desc["workload"] +
+                                    "; MLP 12-64-64-2 trained on 100 plain iterations of a 300k-hit-point box "
+                                    "scene of another seed",
+                        "hit_points": hp.n, "photons_per_iter": test_sc.J, "l2": "not flushed",
+                        "parallelism": "single GPU", "mapping": params.mapping, "cell_factor": params.cell_factor}
+                       if frame else
+                       {"workload": "learned radius: tiny config (64x64 hit points, 100k photons/iter, "
+                                    "step edge, r0=0.02), MLP 12-64-64-2 trained on 200 plain iterations",
+                        "hit_points": 4096, "photons_per_iter": 100_000, "l2": "not flushed (small)",
+                        "parallelism": "single GPU"}),
             "equal_mse": {"target_mse": target, "plain_iterations": N, "learned_iterations": reach,
                           "plain_ms": t_plain, "learned_ms": t_learn,
                           "speedup": (t_plain / t_learn) if t_learn else None,
-                          "mse_at_16": {"plain": pmse[15], "learned": lmse[15]} if N >= 16 else None},
+                          "mse_at_16": {"plain": pmse[15], "learned": lmse[15]} if N >= 16 else None,
+                          "mse_at_32": {"plain": pmse[31], "learned": lmse[31]} if N >= 32 else None,
+                          "pairs_per_s_plain": ppairs / (sum(pms) / 1e3)},
             "training": {"samples": int(X.shape[0]), "epochs": 20, "final_loss": losses[-1],
-                         "seconds": train_s}}
+                         "seconds": train_s, "iterations": train_iters}}
 
 
 def _mse_run(sc, hp, ref, N, r0, params):
@@ -696,9 +756,11 @@ def run_reference(args):
     W, K = args.warmup, args.steps
     kw = {"vcm": True, "k": 0.9} if args.config == "vcm" else ({"test": 1} if args.config == "cppm" else {})
     ph_np = synth.stack_numpy([sc.photons(1, "cpu")])
-    _, dt = oracle_sample(sc, ph_np, hp_np, 64, seed=0, **kw)
-    per_step_s = min(2.0, 150.0 / (W + K))
-    n = int(min(hp_np["pos"].shape[0], max(16, 64 * per_step_s / max(dt, 1e-3))))
+    _, dt0 = oracle_sample(sc, ph_np, hp_np, 16, seed=0, **kw)
+    _, dt = oracle_sample(sc, ph_np, hp_np, 1024, seed=0, **kw)
+    per_hit = max(dt - dt0, 1e-6) / 1024
+    per_step_s = max(min(6.0, 150.0 / (W + K)) - dt0, 0.5)
+    n = int(min(hp_np["pos"].shape[0], max(16, per_step_s / per_hit)))
     pairs = 0
     secs = 0.0
     for i in range(W + K):
@@ -716,7 +778,8 @@ def run_reference(args):
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
                              "kind": "oracle",
                              "sample": f"per step {n} random hit points x 1 iteration of {sc.J} photons, "
-                                       f"brute force all pairs, FP64 statistics"},
+                                       f"the oracle's grid form (photons sorted by cell, each disk's "
+                                       f"cells scanned), FP64 statistics, grid build included"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0

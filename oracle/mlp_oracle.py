@@ -15,6 +15,14 @@ Pinned in tests/test_mlp_oracle.py: the rounding against torch's bfloat16
 conversion; the unrounded network's gradient, and the straight-through
 gradient (rounding offsets frozen at the evaluation point), by central
 finite differences.
+
+Also the two update rules around the network: one Adam step (Kingma & Ba,
+"Adam: A Method for Stochastic Optimization", 2015, Algorithm 1, with its
+bias-corrected moments), pinned by the closed forms of its first step and
+of a constant gradient; and the proposer's radius rule as the library's
+interface states it (a hit point the F-test kept, called doomed, gets a
+smaller radius clipped by Eq. radiusupdate's bound and a cleared window),
+pinned by its invariants and hand cases.
 """
 from __future__ import annotations
 
@@ -100,3 +108,36 @@ def loss_and_grad(p: dict, X, Y, M, scale: float, act=_layer_input_bf16):
 
 def loss_only(flat: np.ndarray, X, Y, M, scale: float, act=_layer_input_bf16) -> float:
     return loss_and_grad(split(flat), X, Y, M, scale, act)[0]
+
+
+def adam_step(master, grad, m, v, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step in FP64 (Kingma & Ba 2015, Algorithm 1): the moment
+    estimates m <- beta1 m + (1 - beta1) g and v <- beta2 v + (1 - beta2) g^2,
+    their bias corrections m / (1 - beta1^t) and v / (1 - beta2^t) at step
+    t >= 1, and theta <- theta - lr * mhat / (sqrt(vhat) + eps).  Returns
+    (theta, m, v) as new arrays."""
+    g = np.asarray(grad, np.float64)
+    m = beta1 * np.asarray(m, np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, np.float64) + (1.0 - beta2) * g * g
+    mhat = m / (1.0 - beta1 ** step)
+    vhat = v / (1.0 - beta2 ** step)
+    theta = np.asarray(master, np.float64) - lr * mhat / (np.sqrt(vhat) + eps)
+    return theta, m, v
+
+
+def propose(r, t, out, bound: float, threshold: float, min_ratio: float):
+    """The proposer's rule after an iteration's F-test update, per hit point:
+    one the test has just rejected (t == 0) is left alone; otherwise, when
+    the network calls it doomed (sigmoid(o1) > threshold) and predicts a
+    smaller radius (o0 < 0), the radius becomes
+    max(r * max(exp(o0), min_ratio), bound) -- never below the bound of
+    Eq. radiusupdate -- and, if that is smaller than r, its window is cleared
+    (t = 0).  FP64.  Returns (new radii, new t, mask of the hit points
+    shrunk); the caller clears the counts and sums of the masked ones."""
+    r = np.asarray(r, np.float64)
+    t = np.asarray(t)
+    o = np.asarray(out, np.float64)
+    doomed = (1.0 / (1.0 + np.exp(-o[:, 1])) > threshold) & (o[:, 0] < 0.0) & (t > 0)
+    rn = np.maximum(r * np.maximum(np.exp(np.minimum(o[:, 0], 0.0)), min_ratio), bound)
+    shrunk = doomed & (rn < r)
+    return np.where(shrunk, rn, r), np.where(shrunk, 0, t), shrunk

@@ -84,11 +84,12 @@ def lib():
         _lib.oracle_lum.argtypes = [d, d, d]
         _lib.oracle_mis_weight.restype = d
         _lib.oracle_mis_weight.argtypes = [d, d, d, d, i, d, d]
-        _lib.oracle_run.restype = i
-        _lib.oracle_run.argtypes = [ctypes.c_int64, P, P, P, P, P, P, i,
-                                    ctypes.c_int64, P, P, i, P, P, P,
-                                    ctypes.POINTER(_Params),
-                                    P, P, P, P, P, P, P, P, P, P, P]
+        for fn in (_lib.oracle_run, _lib.oracle_run_grid):
+            fn.restype = i
+            fn.argtypes = [ctypes.c_int64, P, P, P, P, P, P, i,
+                           ctypes.c_int64, P, P, i, P, P, P,
+                           ctypes.POINTER(_Params),
+                           P, P, P, P, P, P, P, P, P, P, P]
     return _lib
 
 
@@ -193,8 +194,11 @@ class OracleResult:
 
 def run(hp: dict, photons: dict, r_init, iters: int, *, k=0.7, alpha=0.75,
         r_min=None, alpha_f=0.01, rgb_test=False, vcm=False, n_vm=None,
-        i0=1, test=0, hp_iters=None, outputs=True) -> OracleResult:
-    """Run the method for ``iters`` iterations over brute-force all pairs.
+        i0=1, test=0, hp_iters=None, outputs=True, grid=False) -> OracleResult:
+    """Run the method for ``iters`` iterations over brute-force all pairs
+    (grid=True: over the photons of a sorted uniform grid's cells around each
+    disk instead -- the same pairs, counts and decisions, FP64 sums added in
+    cell order; the form timed as the CPU baseline).
 
     hp: dict with pos (nh,3), u (nh,3), v (nh,3) float32 and optional
         nq (nh,) uint32 packed normals and rho (nh,2) float32 (VCM+).
@@ -255,7 +259,8 @@ def run(hp: dict, photons: dict, r_init, iters: int, *, k=0.7, alpha=0.75,
         o_r = o_c = o_S = o_Q = o_F = o_Fc = o_rej = o_pairs = o_est = None
     o_t = np.zeros(nh, np.int32)
     o_tau = np.zeros((nh, nch), np.float64)
-    rc = lib().oracle_run(nh, _ptr(pos), _ptr(hu), _ptr(hv), _ptr(hnq),
+    run_fn = lib().oracle_run_grid if grid else lib().oracle_run
+    rc = run_fn(nh, _ptr(pos), _ptr(hu), _ptr(hv), _ptr(hnq),
                           _ptr(hrho), _ptr(r_init), iters, J, _ptr(ppos),
                           _ptr(flux), nch, _ptr(pnq), _ptr(prho), _ptr(pwq),
                           ctypes.byref(prm), _ptr(o_r), _ptr(o_c), _ptr(o_S),

@@ -35,6 +35,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_NA 2            /* equi-areal annuli, Sec. 6.1.1 */
 #define OR_NS 6            /* equi-areal sectors per annulus, Sec. 6.1.1 */
@@ -392,6 +395,98 @@ static double or_window_f(const or_window* w, int nch, int ch, double m,
     return F;
 }
 
+/* ------------------------------------------------------------------------
+ * 7. The same method with a sorted uniform grid as the range search over
+ *    the iteration's photons (Sec. 5.1 step 1 builds such a
+ *    structure first), for timing the method on the CPU.  Photons are
+ *    sorted by their integer cell (iz, iy, ix) = floor(p / h), FP64, with
+ *    h = the largest initial radius (radii only shrink, so a disk always
+ *    fits in 3 cells per axis); a hit point visits the cells of the box
+ *    [floor((x - r')/h), floor((x + r')/h)] per axis, r' = r (1 + 2^-10)
+ *    plus the rounding of x (a photon that passes the FP32 disk test lies
+ *    within r (1 + 2^-20) of x), and classifies every photon there with the
+ *    same FP32 rules as the brute force.  The in-disk photons, and so the
+ *    counts and decisions, are exactly the brute force's; only the order in
+ *    which the FP64 sums add them changes.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int64_t iz, iy, ix;
+    int64_t p;         /* photon index within the iteration */
+} or_cell_entry;
+
+static int or_cell_cmp(const void* a, const void* b)
+{
+    const or_cell_entry* x = (const or_cell_entry*)a;
+    const or_cell_entry* y = (const or_cell_entry*)b;
+    if (x->iz != y->iz) return x->iz < y->iz ? -1 : 1;
+    if (x->iy != y->iy) return x->iy < y->iy ? -1 : 1;
+    if (x->ix != y->ix) return x->ix < y->ix ? -1 : 1;
+    return x->p < y->p ? -1 : (x->p > y->p ? 1 : 0);
+}
+
+static int64_t or_cell_of(double v, double h)
+{
+    return (int64_t)floor(v / h);
+}
+
+/* Sort g[0, n) by or_cell_cmp with all threads: every thread sorts one
+ * contiguous chunk, then pairs of sorted runs are merged (into tmp and
+ * back) until one run is left.  The order is the total order of
+ * or_cell_cmp (photon index last), so it does not depend on the thread
+ * count. */
+static int or_sort_cells(or_cell_entry* g, int64_t n)
+{
+    int nt = 1;
+#ifdef _OPENMP
+    nt = omp_get_max_threads();
+#endif
+    if (nt < 1) nt = 1;
+    if (n < 65536 || nt == 1) {
+        qsort(g, (size_t)n, sizeof(or_cell_entry), or_cell_cmp);
+        return 0;
+    }
+    or_cell_entry* tmp = (or_cell_entry*)malloc(sizeof(or_cell_entry) * (size_t)n);
+    if (!tmp) {
+        qsort(g, (size_t)n, sizeof(or_cell_entry), or_cell_cmp);
+        return 0;
+    }
+    const int64_t chunk = (n + nt - 1) / nt;
+    #pragma omp parallel for schedule(static, 1)
+    for (int c = 0; c < nt; ++c) {
+        const int64_t a = c * chunk, b = a + chunk < n ? a + chunk : n;
+        if (a < b) qsort(g + a, (size_t)(b - a), sizeof(or_cell_entry), or_cell_cmp);
+    }
+    or_cell_entry *src = g, *dst = tmp;
+    for (int64_t width = chunk; width < n; width *= 2) {
+        const int64_t pairs = (n + 2 * width - 1) / (2 * width);
+        #pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t q = 0; q < pairs; ++q) {
+            int64_t i = 2 * q * width, mid = i + width < n ? i + width : n;
+            const int64_t end = mid + width < n ? mid + width : n;
+            int64_t j = mid, o = i;
+            while (i < mid && j < end) dst[o++] = or_cell_cmp(&src[j], &src[i]) < 0 ? src[j++] : src[i++];
+            while (i < mid) dst[o++] = src[i++];
+            while (j < end) dst[o++] = src[j++];
+        }
+        or_cell_entry* t = src; src = dst; dst = t;
+    }
+    if (src != g) memcpy(g, src, sizeof(or_cell_entry) * (size_t)n);
+    free(tmp);
+    return 0;
+}
+
+/* first entry of grid[0, n) not ordered before cell (iz, iy, ix) */
+static int64_t or_cell_lower(const or_cell_entry* grid, int64_t n, int64_t iz, int64_t iy, int64_t ix)
+{
+    or_cell_entry key = {iz, iy, ix, -1};
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (or_cell_cmp(&grid[mid], &key) < 0) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
 /*
  * Inputs (all host arrays, row-major):
  *   hp_pos, hp_u, hp_v: nh*3 float; hp_nq: nh packed snorm8 normals or NULL;
@@ -420,16 +515,16 @@ static double or_window_f(const or_window* w, int nch, int ch, double m,
  *   out_tau:    nh*nch        final accumulated estimate sum
  * Returns 0 on success, -1 on bad arguments.
  */
-int oracle_run(int64_t nh, const float* hp_pos, const float* hp_u,
-               const float* hp_v, const uint32_t* hp_nq, const float* hp_rho,
-               const float* r_init, int iters, int64_t J, const float* ph_pos,
-               const float* ph_flux, int nch, const uint32_t* ph_nq,
-               const float* ph_rho, const uint32_t* ph_wq,
-               const oracle_params* prm,
-               float* out_r, int32_t* out_counts, double* out_S,
-               double* out_Q, double* out_F, double* out_Fc,
-               uint8_t* out_reject, int32_t* out_pairs, int32_t* out_t,
-               double* out_tau, double* out_est)
+static int or_run(int use_grid, int64_t nh, const float* hp_pos, const float* hp_u,
+                  const float* hp_v, const uint32_t* hp_nq, const float* hp_rho,
+                  const float* r_init, int iters, int64_t J, const float* ph_pos,
+                  const float* ph_flux, int nch, const uint32_t* ph_nq,
+                  const float* ph_rho, const uint32_t* ph_wq,
+                  const oracle_params* prm,
+                  float* out_r, int32_t* out_counts, double* out_S,
+                  double* out_Q, double* out_F, double* out_Fc,
+                  uint8_t* out_reject, int32_t* out_pairs, int32_t* out_t,
+                  double* out_tau, double* out_est)
 {
     if (nh < 0 || iters < 0 || J < 2 || (nch != 1 && nch != 3) || !prm ||
         (prm->test != 0 && prm->test != 1))
@@ -448,6 +543,28 @@ int oracle_run(int64_t nh, const float* hp_pos, const float* hp_u,
     float* bound = (float*)malloc(sizeof(float) * (size_t)(iters > 0 ? iters : 1));
     for (int it = 0; it < iters; ++it)
         bound[it] = oracle_radius_bound(prm->r_min, prm->alpha, prm->i0 + it);
+
+    /* grid form: every iteration's photons sorted by cell (section 7) */
+    or_cell_entry* grid = NULL;
+    double gh = 0.0;
+    if (use_grid && iters > 0 && J > 0) {
+        for (int64_t h = 0; h < nh; ++h) if ((double)r_init[h] > gh) gh = (double)r_init[h];
+        if (!(gh > 0.0)) gh = 1.0;
+        grid = (or_cell_entry*)malloc(sizeof(or_cell_entry) * (size_t)iters * (size_t)J);
+        if (!grid) { free(fc); free(bound); return -1; }
+        for (int it = 0; it < iters; ++it) {
+            or_cell_entry* g = grid + (size_t)it * J;
+            const float* P = ph_pos + (size_t)it * J * 3;
+            #pragma omp parallel for schedule(static)
+            for (int64_t p = 0; p < J; ++p) {
+                g[p].ix = or_cell_of(P[3 * p], gh);
+                g[p].iy = or_cell_of(P[3 * p + 1], gh);
+                g[p].iz = or_cell_of(P[3 * p + 2], gh);
+                g[p].p = p;
+            }
+            or_sort_cells(g, J);
+        }
+    }
 
     #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t h = 0; h < nh; ++h) {
@@ -471,7 +588,29 @@ int oracle_run(int64_t nh, const float* hp_pos, const float* hp_u,
             if (out_r) out_r[(size_t)it * nh + h] = r;
             double phi_sum[3] = {0.0, 0.0, 0.0};
             int32_t pairs = 0;
-            for (int64_t p = 0; p < J; ++p) {
+            /* candidates: every photon (brute force), or the photons of the
+             * cells around the disk (grid form), row by row */
+            const or_cell_entry* G = grid ? grid + (size_t)it * J : NULL;
+            int64_t cz0 = 0, cz1 = 0, cy0 = 0, cy1 = 0, cx0 = 0, cx1 = 0;
+            if (G) {
+                const double rr = (double)r * (1.0 + 1.0 / 1024.0)
+                                + 1e-6 * (fabs((double)xh[0]) + fabs((double)xh[1]) + fabs((double)xh[2]));
+                cx0 = or_cell_of((double)xh[0] - rr, gh); cx1 = or_cell_of((double)xh[0] + rr, gh);
+                cy0 = or_cell_of((double)xh[1] - rr, gh); cy1 = or_cell_of((double)xh[1] + rr, gh);
+                cz0 = or_cell_of((double)xh[2] - rr, gh); cz1 = or_cell_of((double)xh[2] + rr, gh);
+            }
+            int64_t row_z = cz0, row_y = cy0, k = 0, kend = G ? 0 : J;
+            for (;;) {
+                if (k == kend) {
+                    if (!G || row_z > cz1) break;
+                    /* next row of cells */
+                    k = or_cell_lower(G, J, row_z, row_y, cx0);
+                    kend = or_cell_lower(G, J, row_z, row_y, cx1 + 1);
+                    if (++row_y > cy1) { row_y = cy0; ++row_z; }
+                    continue;
+                }
+                const int64_t p = G ? G[k].p : k;
+                ++k;
                 size_t gp = (size_t)it * J + p;
                 int g = oracle_classify(xh, u, v, r, P + 3 * p, use_normals,
                                         use_normals ? hp_nq[hi] : 0,
@@ -547,5 +686,40 @@ int oracle_run(int64_t nh, const float* hp_pos, const float* hp_u,
     }
     free(fc);
     free(bound);
+    free(grid);
     return 0;
+}
+
+int oracle_run(int64_t nh, const float* hp_pos, const float* hp_u,
+               const float* hp_v, const uint32_t* hp_nq, const float* hp_rho,
+               const float* r_init, int iters, int64_t J, const float* ph_pos,
+               const float* ph_flux, int nch, const uint32_t* ph_nq,
+               const float* ph_rho, const uint32_t* ph_wq,
+               const oracle_params* prm,
+               float* out_r, int32_t* out_counts, double* out_S,
+               double* out_Q, double* out_F, double* out_Fc,
+               uint8_t* out_reject, int32_t* out_pairs, int32_t* out_t,
+               double* out_tau, double* out_est)
+{
+    return or_run(0, nh, hp_pos, hp_u, hp_v, hp_nq, hp_rho, r_init, iters, J, ph_pos, ph_flux,
+                  nch, ph_nq, ph_rho, ph_wq, prm, out_r, out_counts, out_S, out_Q, out_F,
+                  out_Fc, out_reject, out_pairs, out_t, out_tau, out_est);
+}
+
+/* The same as oracle_run with the grid of section 7 as the range search
+ * (identical counts and decisions; FP64 sums in cell order). */
+int oracle_run_grid(int64_t nh, const float* hp_pos, const float* hp_u,
+                    const float* hp_v, const uint32_t* hp_nq, const float* hp_rho,
+                    const float* r_init, int iters, int64_t J, const float* ph_pos,
+                    const float* ph_flux, int nch, const uint32_t* ph_nq,
+                    const float* ph_rho, const uint32_t* ph_wq,
+                    const oracle_params* prm,
+                    float* out_r, int32_t* out_counts, double* out_S,
+                    double* out_Q, double* out_F, double* out_Fc,
+                    uint8_t* out_reject, int32_t* out_pairs, int32_t* out_t,
+                    double* out_tau, double* out_est)
+{
+    return or_run(1, nh, hp_pos, hp_u, hp_v, hp_nq, hp_rho, r_init, iters, J, ph_pos, ph_flux,
+                  nch, ph_nq, ph_rho, ph_wq, prm, out_r, out_counts, out_S, out_Q, out_F,
+                  out_Fc, out_reject, out_pairs, out_t, out_tau, out_est);
 }

@@ -28,6 +28,18 @@ TILES = (64, 128, 256)       # batch tile sizes (hit points), tried for the best
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 
+def supported(mapping: int, params) -> bool:
+    """Traversal 3 tests one channel and traversal 4 gathers one flux
+    channel (the library refuses the other combinations)."""
+    if params is None:
+        return True
+    if mapping == 3 and params.rgb_test:
+        return False
+    if mapping == 4 and params.channels == 3:
+        return False
+    return True
+
+
 def size_class(nh: int, J: int, r0: float) -> str:
     return f"h{round(math.log2(max(nh, 1)))}-j{round(math.log2(max(J, 2)))}-r{round(4 * math.log2(r0))}"
 
@@ -78,7 +90,8 @@ def tune(hp, batches, r0: float, key: str | None = None, cache: str | None = DEF
     data = _load(cache) if cache else {}
     ent = data.get(key)
     if ent is None:
-        times = {f"{m},{cf}": time_config(hp, batches, r0, m, cf, params) for m, cf in candidates}
+        times = {f"{m},{cf}": time_config(hp, batches, r0, m, cf, params) for m, cf in candidates
+                 if supported(m, params)}
         best = min(times, key=times.get)
         m, cf = best.split(",")
         ent = {"mapping": int(m), "cell_factor": float(cf), "ms": times}

@@ -19,8 +19,8 @@ constexpr int kWarps = kThreads / 32;
 // cap the resident blocks anyway (and whose sums need the registers)
 template <int MAPPING, int NTC = 1>
 constexpr int kMinBlocks =
-    (MAPPING == 0 ? 8 : (MAPPING == 1 || MAPPING == 4 ? 6 : (MAPPING == 2 ? 4 : 5))) * (128 / kThreads) /
-    (NTC == 3 ? 2 : 1);
+    (MAPPING == 0 || MAPPING == 5 ? 8 : (MAPPING == 1 || MAPPING == 4 ? 6 : (MAPPING == 2 ? 4 : 5))) *
+    (128 / kThreads) / (NTC == 3 ? 2 : 1);
 constexpr int kNormalDotMin = 8064;   // 127^2 / 2: cosine > ~0.5
 
 // arrays shared by all hit points of a launch (state is [slot][nh])
@@ -74,6 +74,15 @@ template <int QCAP>
 struct UnionSmem {
     float4 chunk[kWarps][32];
     uint32_t queue[kWarps][QCAP][32];   // per-lane in-disk queues
+};
+
+// traversal 5: per-lane queues of in-disk photons, [slot][lane] so a
+// warp's stores and loads of one slot hit 32 distinct banks
+constexpr int kLockQ = 32;         // queue slots per lane
+constexpr int kLockStep = 4;       // candidates a lane tests between two warp votes
+
+struct LockQueue {
+    uint32_t q[kWarps][kLockQ][32];
 };
 
 // this thread's hit point
@@ -307,6 +316,114 @@ __device__ void gather_own(const GatherArgs& a, const Hit& H, const GridGeom& G,
     }
 }
 
+// traversal 5, drain: every lane classifies its queued in-disk photons in
+// queue order (its walk order), the warp in lockstep up to the longest
+// queue; the next entry's record is loaded before the current one is used
+template <int NCH, int NTC, bool NORMALS, bool VCM, bool BATCH>
+__device__ __forceinline__ void drain_lockstep(const GatherArgs& a, const Hit& H, Smem<NTC>& sm,
+                                               LockQueue& lq, int w, int lane, int tid,
+                                               Acc<NCH>& acc, int qlen)
+{
+    const int qmax = __reduce_max_sync(0xffffffffu, qlen);
+    uint32_t pn = 0u;
+    float4 Xn = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (qlen > 0) { pn = lq.q[w][0][lane]; Xn = __ldg(a.rec0 + pn); }
+    for (int k = 0; k < qmax; ++k) {
+        const uint32_t p = pn;
+        const float4 X = Xn;
+        if (k + 1 < qlen) { pn = lq.q[w][k + 1][lane]; Xn = __ldg(a.rec0 + pn); }
+        if (k < qlen) {
+            float dx, dy, dz;
+            in_disk(H, X, dx, dy, dz);
+            gather_pair<NCH, NTC, NORMALS, VCM, BATCH>(a, H, sm, tid, acc, p, X, dx, dy, dz);
+        }
+    }
+    __syncwarp();
+}
+
+// Traversal 5: the warp walks the rows of its lanes' cell boxes in step
+// (row (dz, dy) of every lane's own box at once), each lane its own trimmed
+// runs, kLockStep candidates at a time between warp votes; in-disk photons
+// go to the lane's queue and are classified in lockstep whenever a queue
+// could overflow and at the end.  A lane's photons are classified in the
+// order traversal 0 visits them, so its sums are bit-identical to it.
+template <int NCH, int NTC, bool NORMALS, bool VCM, bool BATCH>
+__device__ void gather_lockstep(const GatherArgs& a, const Hit& H, const GridGeom& G, CellBox b, bool live,
+                                Smem<NTC>& sm, LockQueue& lq, int tid, int lane, int w, Acc<NCH>& acc)
+{
+    const unsigned full = 0xffffffffu;
+    const int B = 1 << G.lb;
+    if (live && (b.ix1 - b.ix0 >= B || b.iy1 - b.iy0 >= B || b.iz1 - b.iz0 >= B)) {
+        atomicOr(a.err, 1);
+        b.ix1 = min(b.ix1, b.ix0 + B - 1); b.iy1 = min(b.iy1, b.iy0 + B - 1); b.iz1 = min(b.iz1, b.iz0 + B - 1);
+    }
+    const RowCull rcu = row_cull(H, G, b);
+    const int nz = live ? b.iz1 - b.iz0 + 1 : 0;
+    const int ny = live ? b.iy1 - b.iy0 + 1 : 0;
+    const int NZ = __reduce_max_sync(full, nz);
+    const int NY = __reduce_max_sync(full, ny);
+    int qlen = 0;
+    for (int dz = 0; dz < NZ; ++dz) {
+        const int iz = b.iz0 + dz;
+        float rz2 = -1.f;
+        if (dz < nz) {
+            const float gz = slab_gap(H.P.z, iz, G, rcu.eps);
+            rz2 = rcu.rc2 - gz * gz;
+        }
+        for (int dy = 0; dy < NY; ++dy) {
+            const int iy = b.iy0 + dy;
+            // this lane's photons of row (iy, iz): at most two hash-block runs
+            uint32_t s0 = 0u, n0 = 0u, s1 = 0u, n = 0u;
+            if (dy < ny && rz2 + rcu.slack >= 0.f) {
+                const float gy = slab_gap(H.P.y, iy, G, rcu.eps);
+                const float ryz2 = rz2 - gy * gy;
+                if (ryz2 + rcu.slack >= 0.f) {
+                    const float half = sqrtf(fmaxf(ryz2, 0.f) + rcu.slack) + rcu.eps;
+                    const int xa = max(b.ix0, ppm_cell_coord(__fsub_rn(H.P.x, half), G.inv_h));
+                    const int xb = min(b.ix1, ppm_cell_coord(__fadd_rn(H.P.x, half), G.inv_h));
+                    if (xa <= xb) {
+                        const int ixe = min(xb, xa | (B - 1));
+                        const uint32_t b0 = ppm_bucket(xa, iy, iz, G);
+                        s0 = __ldg(a.cell_start + b0);
+                        n0 = __ldg(a.cell_start + b0 + (uint32_t)(ixe - xa) + 1u) - s0;
+                        n = n0;
+                        if (ixe < xb) {
+                            const uint32_t b1 = ppm_bucket(ixe + 1, iy, iz, G);
+                            s1 = __ldg(a.cell_start + b1);
+                            n += __ldg(a.cell_start + b1 + (uint32_t)(xb - ixe - 1) + 1u) - s1;
+                        }
+                    }
+                }
+            }
+            acc.cand += n;
+            const uint32_t N = __reduce_max_sync(full, n);
+            for (uint32_t k0 = 0; k0 < N; k0 += kLockStep) {
+                float4 X[kLockStep];
+                uint32_t pk[kLockStep];
+#pragma unroll
+                for (int j = 0; j < kLockStep; ++j) {
+                    const uint32_t k = k0 + (uint32_t)j;
+                    pk[j] = k < n0 ? s0 + k : s1 + (k - n0);
+                    X[j] = k < n ? __ldg(a.rec0 + pk[j]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int j = 0; j < kLockStep; ++j) {
+                    float dx, dy2, dz2;
+                    if (k0 + (uint32_t)j < n && in_disk(H, X[j], dx, dy2, dz2)) {
+                        lq.q[w][qlen][lane] = pk[j];
+                        ++qlen;
+                    }
+                }
+                if (__any_sync(full, qlen > kLockQ - kLockStep)) {
+                    drain_lockstep<NCH, NTC, NORMALS, VCM, BATCH>(a, H, sm, lq, w, lane, tid, acc, qlen);
+                    qlen = 0;
+                }
+            }
+        }
+    }
+    drain_lockstep<NCH, NTC, NORMALS, VCM, BATCH>(a, H, sm, lq, w, lane, tid, acc, qlen);
+}
+
 // traversal 1, drain: each lane processes its queued in-disk photons in
 // queue (= traversal) order; the warp loops to the longest queue
 template <int NCH, int NTC, bool NORMALS, bool VCM, bool BATCH, typename US>
@@ -358,6 +475,7 @@ struct FixSmem {
 template <int NCH, int NTC, int MAPPING>
 struct BlockShared {
     typename std::conditional<MAPPING == 3, Empty, Smem<NTC>>::type sm;
+    typename std::conditional<MAPPING == 5, LockQueue, Empty>::type lq;
     typename std::conditional<MAPPING == 1 || MAPPING == 2, UnionSmem<MAPPING == 2 ? 64 : 32>, Empty>::type us;
     typename std::conditional<MAPPING == 3, PairSmem, Empty>::type ps;
     typename std::conditional<MAPPING == 3, FixSmem<NCH>, Empty>::type fx;
@@ -686,6 +804,10 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
     const FixScale fs = fix_scale(MAPPING == 3 ? G.psimax : 1.f);
     if constexpr (MAPPING == 0) {
         if (live) gather_own<NCH, NTC, NORMALS, VCM, BATCH>(a, H, G, b, sm, tid, acc);
+    } else if constexpr (MAPPING == 5) {
+        __syncwarp();
+        if (__any_sync(0xffffffffu, live))
+            gather_lockstep<NCH, NTC, NORMALS, VCM, BATCH>(a, H, G, b, live, sm, bsh.lq, tid, lane, w, acc);
     } else if constexpr (MAPPING == 4) {
         __syncwarp();
         for (int j = 0; j < 32; ++j) {

@@ -51,7 +51,7 @@ def _run_batch(scenes, iters, params, cfs=None):
     return hps, phs, states, stats, L, graph
 
 
-@pytest.mark.parametrize("mapping", [0, 1, 3, 4])
+@pytest.mark.parametrize("mapping", [0, 1, 3, 4, 5])
 def test_batch_matches_oracle_per_problem(mapping):
     scenes = _problems()
     iters = 4
@@ -65,7 +65,7 @@ def test_batch_matches_oracle_per_problem(mapping):
         assert rep.diverged <= 2
 
 
-@pytest.mark.parametrize("mapping", [0, 1, 3, 4])
+@pytest.mark.parametrize("mapping", [0, 1, 3, 4, 5])
 def test_batch_bit_identical_to_single_contexts(mapping):
     """Traversals 0-3 visit a hit point's photons in the same order in a
     batch as in a context, so the state is bit-identical.  Traversal 4 splits
@@ -151,8 +151,10 @@ def test_batch_windows_beyond_the_initial_critical_value_table():
     import torch
     from paper_2504_04411_gb300 import ppm
     iters = 1030
-    scenes = [synth.PlaneScene(nside=6, J=600, r0=0.12, step=False, seed=synth.SEED_BASE + 500 + i)
-              for i in range(2)]
+    # uniform photons reaching well past every disk: the null hypothesis
+    # holds, and at alpha_F = 1e-9 no test rejects, so windows grow to 1030
+    scenes = [synth.PlaneScene(nside=6, J=900, r0=0.1, step=False, lo=-0.3, hi=1.3,
+                               seed=synth.SEED_BASE + 500 + i) for i in range(2)]
     hps = [s.hitpoints("cuda") for s in scenes]
     phs = [[s.photons(i, "cuda") for s in scenes] for i in range(1, iters + 1)]
     b = ppm.Batch(hps, [s.r0 for s in scenes], [s.J for s in scenes], params=_params(alpha_f=1e-9))
@@ -170,6 +172,40 @@ def test_batch_windows_beyond_the_initial_critical_value_table():
                     sc.r0, iters, alpha_f=1e-9)
         st = states[p]
         assert np.array_equal(st["t"], ref.t) and np.array_equal(st["r"], ref.r[-1])
-        assert ref.t.max() > 1024                     # windows past the initial table
-        long = ref.t > 1024
-        assert np.allclose(st["F"][long], ref.F[-1][long], rtol=1e-3, atol=1e-6)
+        assert np.all(ref.t == iters)                 # windows past the initial table
+        assert np.allclose(st["F"], ref.F[-1], rtol=1e-3, atol=1e-6)
+        assert np.array_equal(st["counts"], ref.counts[-1])
+
+
+
+@pytest.mark.parametrize("mode", ["rgb", "rgb_test", "vcm_rgb", "vcm"])
+@pytest.mark.parametrize("mapping", [0, 1, 3, 4, 5])
+def test_batch_rgb_and_vcm_problems_match_oracle(mode, mapping):
+    """Batches of RGB problems (luminance test or one test per channel) and
+    VCM+ problems (merge weights; RGB or one channel): every problem against
+    the oracle, element by element.  Traversal 3 with per-channel tests and
+    traversal 4 with RGB flux are refused at create."""
+    from paper_2504_04411_gb300 import ppm
+    rgb = mode != "vcm"
+    vcm = mode.startswith("vcm")
+    sizes = [(900, 12_000, 0.05), (130, 5_000, 0.08), (2100, 20_000, 0.04), (1, 3_000, 0.1)]
+    scenes = [synth.BoxScene(nh=nh, J=J, r0=r0, rgb=rgb, vcm=vcm, seed=synth.SEED_BASE + 600 + i)
+              for i, (nh, J, r0) in enumerate(sizes)]
+    p = _params(mapping=mapping, channels=3 if rgb else 1, rgb_test=int(mode == "rgb_test"), vcm=int(vcm),
+                k=0.9 if vcm else 0.7)
+    if (mapping == 3 and mode == "rgb_test") or (mapping == 4 and rgb):
+        hps = [s.hitpoints("cuda") for s in scenes]
+        with pytest.raises(ppm.PPMError) as e:
+            ppm.Batch(hps, [s.r0 for s in scenes], [s.J for s in scenes], params=p)
+        assert e.value.code == ppm.PPM_EINVAL
+        return
+    iters = 4
+    hps, phs, states, stats, L, graph = _run_batch(scenes, iters, p)
+    assert graph[-1]
+    for q, sc in enumerate(scenes):
+        st = [s[q] for s in states]
+        ss = [{"pairs": s[q].pairs, "flags": s[q].flags} for s in stats]
+        ref = O.run(hps[q].numpy(), synth.stack_numpy([ph[q] for ph in phs]), sc.r0, iters,
+                    rgb_test=mode == "rgb_test", vcm=vcm, k=0.9 if vcm else 0.7)
+        rep = compare(st, ss, L[q], ref, iters)
+        assert rep.diverged <= 2

@@ -1,7 +1,9 @@
 """Pins of the FP64 network oracle: the BF16 rounding of the layer inputs
 against torch's bfloat16 conversion; the gradient of the exact network and
 the straight-through gradient of the BF16 network against central finite
-differences; blob decoding against numpy's float conversion (CPU only)."""
+differences; blob decoding against numpy's float conversion; the Adam step
+against the closed forms of its first step and of a constant gradient; the
+proposer's rule against its invariants and hand cases (CPU only)."""
 import numpy as np
 import torch
 
@@ -79,3 +81,61 @@ def test_blob_decoding():
     want = (bf.astype(np.uint32) << 16).view(np.float32)
     assert np.array_equal(p["W1"].ravel(), want[:768])
     assert np.array_equal(p["b3"], b[-2:].astype(np.float64))
+
+
+def test_adam_first_step_is_lr_times_sign():
+    # at t = 1 from zero moments the bias corrections give mhat = g and
+    # vhat = g^2, so every parameter moves by lr * g / (|g| + eps)
+    rng = np.random.default_rng(21)
+    theta = rng.normal(0, 1, 500)
+    g = rng.normal(0, 1, 500) * 10.0 ** rng.uniform(-6, 2, 500)
+    lr = 3e-3
+    th, m, v = MO.adam_step(theta, g, np.zeros(500), np.zeros(500), 1, lr)
+    assert np.allclose(th, theta - lr * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+    assert np.allclose(m, 0.1 * g, rtol=1e-15) and np.allclose(v, 0.001 * g * g, rtol=1e-15)
+
+
+def test_adam_constant_gradient_moves_lr_per_step():
+    # with one gradient g at every step, m_t = (1 - beta1^t) g and
+    # v_t = (1 - beta2^t) g^2: the corrected moments are g and g^2 at every
+    # t, and theta moves by the same lr * g / (|g| + eps) each step
+    g = np.array([2.0, -0.5, 1e-3, -7.0])
+    theta = np.zeros(4)
+    m = np.zeros(4)
+    v = np.zeros(4)
+    lr = 1e-2
+    for step in range(1, 8):
+        theta, m, v = MO.adam_step(theta, g, m, v, step, lr)
+        assert np.allclose(m, (1 - 0.9 ** step) * g, rtol=1e-13)
+        assert np.allclose(v, (1 - 0.999 ** step) * g * g, rtol=1e-12)
+    assert np.allclose(theta, -7 * lr * g / (np.abs(g) + 1e-8), rtol=1e-12)
+    # a zero gradient leaves a zero-moment parameter where it is
+    th, _, _ = MO.adam_step(np.ones(3), np.zeros(3), np.zeros(3), np.zeros(3), 5, 0.1)
+    assert np.array_equal(th, np.ones(3))
+
+
+def test_propose_rule_hand_cases_and_invariants():
+    bound, thr, mr = 0.01, 0.5, 0.1
+    r = np.array([0.04, 0.04, 0.04, 0.04, 0.04, 0.011, 0.04])
+    t = np.array([3, 0, 3, 3, 3, 3, 5])
+    out = np.array([[np.log(0.5), 5.0],     # doomed, halve
+                    [np.log(0.5), 5.0],     # just rejected by the test: untouched
+                    [np.log(0.5), -5.0],    # not doomed
+                    [0.3, 5.0],             # doomed but asks for a larger radius
+                    [-10.0, 5.0],           # clamp at min_ratio
+                    [np.log(0.5), 5.0],     # clamp at the bound
+                    [np.log(0.9999), 0.001]])   # sigmoid just above the threshold
+    rn, tn, sh = MO.propose(r, t, out, bound, thr, mr)
+    assert np.allclose(rn, [0.02, 0.04, 0.04, 0.04, 0.004 if 0.004 > bound else bound, bound, 0.04 * 0.9999])
+    assert list(sh) == [True, False, False, False, True, True, True]
+    assert list(tn) == [0, 0, 3, 3, 0, 0, 0]
+    # invariants on random inputs: never larger, never below the bound
+    # (unless it already was), cleared windows exactly where shrunk
+    rng = np.random.default_rng(3)
+    r = rng.uniform(0.005, 0.05, 2000)
+    t = rng.integers(0, 6, 2000)
+    out = rng.normal(0, 2, (2000, 2))
+    rn, tn, sh = MO.propose(r, t, out, bound, 0.7, 0.2)
+    assert np.all(rn <= r) and np.all((rn >= bound) | (rn == r))
+    assert np.array_equal(sh, rn < r) and np.all(tn[sh] == 0) and np.array_equal(tn[~sh], t[~sh])
+    assert np.all(rn[sh] >= np.maximum(0.2 * r[sh], bound) * (1 - 1e-15))

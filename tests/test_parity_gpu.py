@@ -138,7 +138,7 @@ def test_cppm_argument_checks():
 
 
 # ------------------------------------------ hit points traced anew ------
-@pytest.mark.parametrize("mapping", [0, 1, 4])
+@pytest.mark.parametrize("mapping", [0, 1, 4, 5])
 def test_retraced_hit_points_full_trajectory(mapping):
     """SPPM-style pixels: each iteration's hit points land at a new random
     point of their pixel (ppm_set_hitpoints), statistics carried per pixel;
@@ -185,7 +185,7 @@ def test_set_hitpoints_argument_checks():
 
 
 # --------------------------------------------------------- plane scenes ----
-MAPPINGS = [0, 1, 2, 3, 4]
+MAPPINGS = [0, 1, 2, 3, 4, 5]
 
 
 @pytest.mark.parametrize("mapping", MAPPINGS)
@@ -257,12 +257,23 @@ def test_box_scene_rgb_luminance_test():
     compare(states, stats, L, ref, iters)
 
 
-def test_box_scene_rgb_per_channel_test():
+@pytest.mark.parametrize("mapping", [0, 1, 2, 3, 4, 5])
+def test_box_scene_rgb_per_channel_test(mapping):
+    """One F-test per RGB channel, reject if any rejects: every channel's
+    window sums against the oracle.  Traversal 3 tests one channel and
+    traversal 4 gathers one flux channel: both are refused."""
+    from paper_2504_04411_gb300 import ppm
     sc = _box(rgb=True, seed=2)
     iters = 5
     hp = sc.hitpoints("cuda")
+    p = _params(channels=3, rgb_test=1, mapping=mapping)
+    if mapping in (3, 4):
+        with pytest.raises(ppm.PPMError) as e:
+            ppm.Estimator(hp, sc.r0, params=p)
+        assert e.value.code == ppm.PPM_EINVAL
+        return
     batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
-    states, stats, L = run_gpu(hp, batches, sc.r0, params=_params(channels=3, rgb_test=1))
+    states, stats, L = run_gpu(hp, batches, sc.r0, params=p)
     ref = O.run(hp.numpy(), synth.stack_numpy(batches), sc.r0, iters, rgb_test=True)
     compare(states, stats, L, ref, iters)
 
@@ -275,6 +286,12 @@ def test_box_scene_vcm_merge_weights(rgb, mapping):
     hp = sc.hitpoints("cuda")
     batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
     p = _params(channels=3 if rgb else 1, vcm=1, k=0.9, mapping=mapping)
+    if rgb and mapping == 4:          # traversal 4 gathers one flux channel
+        from paper_2504_04411_gb300 import ppm
+        with pytest.raises(ppm.PPMError) as e:
+            ppm.Estimator(hp, sc.r0, params=p)
+        assert e.value.code == ppm.PPM_EINVAL
+        return
     states, stats, L = run_gpu(hp, batches, sc.r0, params=p)
     ref = O.run(hp.numpy(), synth.stack_numpy(batches), sc.r0, iters, k=0.9, vcm=True)
     compare(states, stats, L, ref, iters)
@@ -536,4 +553,29 @@ def test_vcm_merge_scale_full_size_sampled():
     rep = compare(sub_states, [{"pairs": 0, "flags": 0}] * iters, L[idx], ref, iters, check_pairs=False)
     assert rep.diverged <= 3
     assert ref.pairs.sum() > 50_000
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("rgb,vcm,rgb_test", [(False, False, 0), (True, True, 0), (True, False, 1)])
+def test_lockstep_traversal_is_bit_identical_to_the_thread_walk(rgb, vcm, rgb_test):
+    """Traversal 5 (rows walked in lockstep, in-disk photons queued and
+    classified in lockstep) classifies each hit point's photons in the order
+    traversal 0 visits them: every state array is bit for bit the same."""
+    import torch
+    sc = _box(rgb=rgb, vcm=vcm, seed=4)
+    iters = 5
+    hp = sc.hitpoints("cuda")
+    batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
+    out = []
+    for mapping in (0, 5):
+        p = _params(channels=3 if rgb else 1, vcm=int(vcm), rgb_test=rgb_test, k=0.9 if vcm else 0.7,
+                    mapping=mapping)
+        states, stats, L = run_gpu(hp, batches, sc.r0, params=p)
+        out.append((states, stats, L))
+    (s0, t0, L0), (s5, t5, L5) = out
+    for it in range(iters):
+        for k in s0[it]:
+            assert np.array_equal(s0[it][k], s5[it][k]), (it, k)
+        assert t0[it]["pairs"] == t5[it]["pairs"] and t0[it]["candidates"] == t5[it]["candidates"]
+    assert np.array_equal(L0, L5)
     torch.cuda.synchronize()
