@@ -368,6 +368,7 @@ int launch_batch_gather(ppm_batch* b, const GatherArgs& a, const BatchArgs& bt)
     if (m == 1) k_batch_gather<NCH, NTC, NORMALS, VCM, 1><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
     else if (m == 2) k_batch_gather<NCH, NTC, NORMALS, VCM, 2><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
     else if (m == 5) k_batch_gather<NCH, NTC, NORMALS, VCM, 5><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
+    else if (m == 6) k_batch_gather<NCH, NTC, NORMALS, VCM, 6><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
     else if (m == 3 && NTC == 1) k_batch_gather<NCH, 1, NORMALS, VCM, 3><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
     else if (m == 4 && NCH == 1) launch_batch_warp_per_hit<NCH, NTC, NORMALS, VCM>(b, a, bt);
     else k_batch_gather<NCH, NTC, NORMALS, VCM, 0><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
@@ -384,6 +385,7 @@ int gather_occupancy(ppm_batch* b)
     if (m == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gather<NCH, NTC, NORMALS, VCM, 1>, kThreads, 0);
     else if (m == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gather<NCH, NTC, NORMALS, VCM, 2>, kThreads, 0);
     else if (m == 5) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gather<NCH, NTC, NORMALS, VCM, 5>, kThreads, 0);
+    else if (m == 6) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gather<NCH, NTC, NORMALS, VCM, 6>, kThreads, 0);
     else if (m == 3 && NTC == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gather<NCH, 1, NORMALS, VCM, 3>, kThreads, 0);
     else if (m == 4 && NCH == 1) e = batch_warp_per_hit_occupancy<NCH, NTC, NORMALS, VCM>(&per_sm);
     else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gather<NCH, NTC, NORMALS, VCM, 0>, kThreads, 0);
@@ -399,7 +401,9 @@ int run_gather(ppm_batch* b)
     a.r = b->r; a.t = b->t; a.F = b->F; a.tau = b->tau;
     a.cnt = b->cnt; a.S = b->S; a.Q = b->Q;
     a.cell_start = b->cell_start;
-    a.rec0 = b->rec0; a.rec1 = b->rec1; a.aux = b->aux;
+    // batches always carry the aux record: with rec1 the two sit side by side
+    a.rec0 = b->rec0; a.rec1 = b->rec1;
+    a.aux = (b->nch == 3 || b->prm.vcm) ? reinterpret_cast<const uint4*>(b->rec1 + 1) : b->aux;
     a.err = b->err;
     a.feat = nullptr;
     BatchArgs bt;
@@ -560,7 +564,7 @@ int ppm_batch_create(int32_t n_problems, const ppm_hitpoints* hp, const float* r
     if (!(prm.rmin_ratio >= 0.f && prm.rmin_ratio < 1.f)) return PPM_EINVAL;
     if (prm.channels != 1 && prm.channels != 3) return PPM_EINVAL;
     if (prm.rgb_test && prm.channels != 3) return PPM_EINVAL;
-    if (prm.mapping < 0 || prm.mapping > 5 || prm.n_vm < 0.f) return PPM_EINVAL;
+    if (prm.mapping < 0 || prm.mapping > 6 || prm.n_vm < 0.f) return PPM_EINVAL;
     if ((prm.mapping == 3 && prm.rgb_test) || (prm.mapping == 4 && prm.channels == 3)) return PPM_EINVAL;
     if (prm.test != 0) return PPM_EINVAL;   // the count test runs in contexts only
     if (prm.tile < 0 || prm.tile > 1024 || prm.tile % kThreads != 0) return PPM_EINVAL;
@@ -619,7 +623,7 @@ int ppm_batch_create(int32_t n_problems, const ppm_hitpoints* hp, const float* r
               dal(&b->pairs_total, P) && dal(&b->head, 1) && dal(&b->ptab_d, P) && dal(&b->sc_d, 1) &&
               dal(&b->err, 1) && dal(&b->rec0, np) && dal(&b->aux, np) &&
               dal(&b->pack, np * ((b->nch == 3 || prm.vcm) ? 3 : 2));
-    if (ok && (b->nch == 3 || prm.vcm)) ok = dal(&b->rec1, np);
+    if (ok && (b->nch == 3 || prm.vcm)) ok = dal(&b->rec1, 2 * np);   // rec1 | aux side by side
     if (ok) ok = cudaMallocHost(&b->ptab_h, P * sizeof(PhotonPtrs)) == cudaSuccess &&
                  cudaMallocHost(&b->sc_h, sizeof(IterScalars)) == cudaSuccess;
     if (ok) ok = ppm_sort_scratch_reserve(&b->sort, np > 0 ? np : 1) == PPM_OK;

@@ -83,6 +83,8 @@ int launch_gather(ppm_ctx* c, const GatherArgs& a, const Prob& pr)
         k_gather_update<NCH, NTC, NORMALS, VCM, 2><<<nb, kThreads, 0, c->stream>>>(a, pr);
     else if (m == 5)
         k_gather_update<NCH, NTC, NORMALS, VCM, 5><<<nb, kThreads, 0, c->stream>>>(a, pr);
+    else if (m == 6)
+        k_gather_update<NCH, NTC, NORMALS, VCM, 6><<<nb, kThreads, 0, c->stream>>>(a, pr);
     else if (m == 3 && NTC == 1)   // traversal 3 tests one channel
         k_gather_update<NCH, 1, NORMALS, VCM, 3><<<nb, kThreads, 0, c->stream>>>(a, pr);
     else if (m == 4 && NCH == 1)   // traversal 4 gathers one flux channel
@@ -104,7 +106,9 @@ int ppm_gather_launch(ppm_ctx* c, float bound)
     a.r = c->r; a.t = c->t; a.F = c->F; a.tau = c->tau;
     a.cnt = c->cnt; a.S = c->S; a.Q = c->Q;
     a.cell_start = c->cell_start;
-    a.rec0 = c->rec0; a.rec1 = c->rec1; a.aux = c->aux;
+    // with both rec1 and aux records the grid keeps them side by side in rec1
+    a.rec0 = c->rec0; a.rec1 = c->rec1;
+    a.aux = ((c->nch == 3 || c->prm.vcm) && c->ph_aux) ? reinterpret_cast<const uint4*>(c->rec1 + 1) : c->aux;
     a.err = c->err_dev;
     a.feat = c->feat;
     Prob pr;

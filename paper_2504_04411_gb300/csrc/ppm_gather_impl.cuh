@@ -19,9 +19,24 @@ constexpr int kWarps = kThreads / 32;
 // cap the resident blocks anyway (and whose sums need the registers)
 template <int MAPPING, int NTC = 1>
 constexpr int kMinBlocks =
-    (MAPPING == 0 || MAPPING == 5 ? 8 : (MAPPING == 1 || MAPPING == 4 ? 6 : (MAPPING == 2 ? 4 : 5))) *
+    (MAPPING == 0 || MAPPING == 5 ? 8 : (MAPPING == 1 || MAPPING == 4 || MAPPING == 6 ? 6 : (MAPPING == 2 ? 4 : 5))) *
     (128 / kThreads) / (NTC == 3 ? 2 : 1);
 constexpr int kNormalDotMin = 8064;   // 127^2 / 2: cosine > ~0.5
+
+// rec1 and aux of an in-disk photon: side by side (aux = rec1 + 1, a stride
+// of 2 float4) when a launch uses both, else each in its own array
+template <int NCH, bool NORMALS, bool VCM, bool BATCH>
+constexpr int kSideStride = ((NCH == 3 || VCM) && (NORMALS || VCM || BATCH)) ? 2 : 1;
+
+// 1 / x for the merge weight's denominator x >= 1: the hardware's
+// approximate reciprocal (relative error below 2^-22); the weight scales a
+// sum that the tests hold to 2e-5, and no decision depends on it alone
+__device__ __forceinline__ float rcp_weight(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // arrays shared by all hit points of a launch (state is [slot][nh])
 struct GatherArgs {
@@ -85,6 +100,17 @@ struct LockQueue {
     uint32_t q[kWarps][kLockQ][32];
 };
 
+// traversal 6: per warp, the current hit point's non-empty runs of photons
+// (rows of its cell box set up by the lanes in parallel) and the in-disk
+// photons found but not yet classified, compacted: (offsets, psi) and index
+constexpr int kMaxRuns = 128;      // 8 x 8 rows of a cell box, two hash-block runs each
+struct WarpHitSmem {
+    uint32_t run_s[kMaxRuns];
+    uint32_t run_n[kMaxRuns];
+    float4 pd[64];                 // (dx, dy, dz, psi) of a queued pair
+    uint32_t pp[64];               // its photon index
+};
+
 // this thread's hit point
 struct Hit {
     float4 P, U, V;
@@ -92,23 +118,38 @@ struct Hit {
     uint32_t nqh, pid;
 };
 
-// RGB flux of this hit point when only its luminance is tested:
-// Kahan-compensated FP32 sums (a disk can hold thousands of photons; plain
-// FP32 summation would drift past 1e-5).  Otherwise Phi_i is the sum of the
-// tested group sums.
+// RGB flux of this hit point when only its luminance is tested: the terms
+// of one run of photons (one hash-block run of a row, or one drained queue)
+// are added in plain FP32, and each run's sum is added to the total with
+// Kahan compensation (a disk can hold thousands of photons: one plain FP32
+// sum over all of them would drift towards 1e-5).  Otherwise Phi_i is the
+// sum of the tested group sums.
 template <int NCH>
 struct Acc {
     float phi[NCH];
     float comp[NCH];
+    float part[NCH];
     unsigned long long cand = 0;
-    __device__ __forceinline__ void add(int c, float v)
+    __device__ __forceinline__ void add(int c, float v) { part[c] = __fadd_rn(part[c], v); }
+    __device__ __forceinline__ void flush()
     {
-        const float y = __fsub_rn(v, comp[c]);
-        const float t = __fadd_rn(phi[c], y);
-        comp[c] = __fsub_rn(__fsub_rn(t, phi[c]), y);
-        phi[c] = t;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            const float y = __fsub_rn(part[c], comp[c]);
+            const float t = __fadd_rn(phi[c], y);
+            comp[c] = __fsub_rn(__fsub_rn(t, phi[c]), y);
+            phi[c] = t;
+            part[c] = 0.f;
+        }
     }
 };
+
+// flush a run's RGB sums where they are kept (luminance test of RGB flux)
+template <int NCH, int NTC>
+__device__ __forceinline__ void flush_run(Acc<NCH>& acc)
+{
+    if constexpr (NCH == 3 && NTC == 1) acc.flush();
+}
 
 __device__ __forceinline__ float warp_max(float v)
 {
@@ -155,7 +196,8 @@ __device__ __forceinline__ void gather_pair(const GatherArgs& a, const Hit& H, S
                                             float dx, float dy, float dz)
 {
     uint4 A = make_uint4(0u, 0u, 0u, 0u);
-    if constexpr (NORMALS || VCM || BATCH) A = __ldg(a.aux + p);
+    constexpr int SIDE = kSideStride<NCH, NORMALS, VCM, BATCH>;
+    if constexpr (NORMALS || VCM || BATCH) A = __ldg(a.aux + (size_t)p * SIDE);
     if constexpr (BATCH) {
         if (A.w != H.pid) return;      // a photon of another problem sharing the bucket
     }
@@ -167,13 +209,13 @@ __device__ __forceinline__ void gather_pair(const GatherArgs& a, const Hit& H, S
     const int g = pair_group(yu, yv, H.r2);
     float w = 1.f;
     float4 X1 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if constexpr (NCH == 3 || VCM) X1 = __ldg(a.rec1 + p);
+    if constexpr (NCH == 3 || VCM) X1 = __ldg(a.rec1 + (size_t)p * SIDE);
     if constexpr (VCM) {
         const int cd = __dp4a((int)A.y, (int)H.nqh, 0);
         const float cosl = cd > 0 ? __fmul_rn((float)cd, 1.0f / 16129.0f) : 0.f;
         const float r_vm = fmaf(H.U.w, __fmul_rn(cosl, 0.318309886f), X1.w);
         const float r_vc = __fadd_rn(H.V.w, __uint_as_float(A.z));
-        w = __frcp_rn(1.f + r_vm + r_vc * H.inv_eta);
+        w = rcp_weight(1.f + r_vm + r_vc * H.inv_eta);
     }
     sm.c[g][tid] += 1u;
     if constexpr (NTC == 1) {
@@ -310,6 +352,7 @@ __device__ void gather_own(const GatherArgs& a, const Hit& H, const GridGeom& G,
                     if (in_disk(H, X, dx, dy, dz))
                         gather_pair<NCH, NTC, NORMALS, VCM, BATCH>(a, H, sm, tid, acc, p, X, dx, dy, dz);
                 }
+                if (e > s) flush_run<NCH, NTC>(acc);
                 ix = ixe + 1;
             }
         }
@@ -338,6 +381,7 @@ __device__ __forceinline__ void drain_lockstep(const GatherArgs& a, const Hit& H
             gather_pair<NCH, NTC, NORMALS, VCM, BATCH>(a, H, sm, tid, acc, p, X, dx, dy, dz);
         }
     }
+    flush_run<NCH, NTC>(acc);
     __syncwarp();
 }
 
@@ -441,6 +485,7 @@ __device__ __forceinline__ void drain_queue(const GatherArgs& a, const Hit& H, S
             gather_pair<NCH, NTC, NORMALS, VCM, BATCH>(a, H, sm, tid, acc, p, X, dx, dy, dz);
         }
     }
+    flush_run<NCH, NTC>(acc);
     qlen = 0;
     __syncwarp();
 }
@@ -479,7 +524,8 @@ struct BlockShared {
     typename std::conditional<MAPPING == 1 || MAPPING == 2, UnionSmem<MAPPING == 2 ? 64 : 32>, Empty>::type us;
     typename std::conditional<MAPPING == 3, PairSmem, Empty>::type ps;
     typename std::conditional<MAPPING == 3, FixSmem<NCH>, Empty>::type fx;
-    typename std::conditional<MAPPING == 4, Smem<NTC>, Empty>::type lp;   // lanes' partial sums
+    typename std::conditional<MAPPING == 4 || MAPPING == 6, Smem<NTC>, Empty>::type lp;   // lanes' partial sums
+    typename std::conditional<MAPPING == 6, WarpHitSmem[kWarps], Empty>::type wh;
 };
 
 // this iteration's sums of one hit point, read where they are kept
@@ -535,7 +581,8 @@ __device__ __forceinline__ void gather_pair_fix(const GatherArgs& a, const Hit& 
                                                 float dx, float dy, float dz)
 {
     uint4 A = make_uint4(0u, 0u, 0u, 0u);
-    if constexpr (NORMALS || VCM || BATCH) A = __ldg(a.aux + p);
+    constexpr int SIDE = kSideStride<NCH, NORMALS, VCM, BATCH>;
+    if constexpr (NORMALS || VCM || BATCH) A = __ldg(a.aux + (size_t)p * SIDE);
     if constexpr (BATCH) {
         if (A.w != H.pid) return;
     }
@@ -547,13 +594,13 @@ __device__ __forceinline__ void gather_pair_fix(const GatherArgs& a, const Hit& 
     const int g = pair_group(yu, yv, H.r2);
     float w = 1.f;
     float4 X1 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if constexpr (NCH == 3 || VCM) X1 = __ldg(a.rec1 + p);
+    if constexpr (NCH == 3 || VCM) X1 = __ldg(a.rec1 + (size_t)p * SIDE);
     if constexpr (VCM) {
         const int cd = __dp4a((int)A.y, (int)H.nqh, 0);
         const float cosl = cd > 0 ? __fmul_rn((float)cd, 1.0f / 16129.0f) : 0.f;
         const float r_vm = fmaf(H.U.w, __fmul_rn(cosl, 0.318309886f), X1.w);
         const float r_vc = __fadd_rn(H.V.w, __uint_as_float(A.z));
-        w = __frcp_rn(1.f + r_vm + r_vc * H.inv_eta);
+        w = rcp_weight(1.f + r_vm + r_vc * H.inv_eta);
     }
     const float psi = VCM ? __fmul_rn(w, X.w) : X.w;
     const float q = psi * fs.t;
@@ -731,6 +778,147 @@ __device__ __forceinline__ void gather_warp_hit(const GatherArgs& a, const Hit& 
     if ((lane & 1) == 0 && (lane >> 1) < PPM_NG) sm.c[lane >> 1][owner] = ct;
 }
 
+// Traversal 6: hit point Hj (lane j's, owner thread `owner`) by the whole
+// warp.  The lanes set up the rows of its cell box in parallel (one row a
+// lane) and list the non-empty runs in row order; the warp then tests 32
+// consecutive candidates a step and compacts the in-disk ones into a queue,
+// and whenever 32 are queued every lane classifies one of them into its own
+// column of lp (so the classification runs with all lanes busy).  At the end
+// the columns are reduced over the warp into the owner's slots of sm; the
+// RGB flux sums of a luminance test go to the owner's acc.
+template <int NCH, int NTC, bool NORMALS, bool VCM, bool BATCH>
+__device__ __forceinline__ void gather_warp_hit_compact(const GatherArgs& a, const Hit& Hj, const GridGeom& G,
+                                                        CellBox b, Smem<NTC>& lp, Smem<NTC>& sm,
+                                                        WarpHitSmem& wh, int tid, int lane, int owner,
+                                                        Acc<NCH>& acc)
+{
+    const unsigned full = 0xffffffffu;
+    const unsigned lt = (1u << lane) - 1u;
+    const int B = 1 << G.lb;
+    if (b.ix1 - b.ix0 >= B || b.iy1 - b.iy0 >= B || b.iz1 - b.iz0 >= B) {
+        if (lane == 0) atomicOr(a.err, 1);
+        b.ix1 = min(b.ix1, b.ix0 + B - 1); b.iy1 = min(b.iy1, b.iy0 + B - 1); b.iz1 = min(b.iz1, b.iz0 + B - 1);
+    }
+    const RowCull rcu = row_cull(Hj, G, b);
+    const int ny = b.iy1 - b.iy0 + 1;
+    const int nrows = ny * (b.iz1 - b.iz0 + 1);
+    // runs of the rows, (iz, iy) in the order traversal 0 visits them
+    int nruns = 0;
+    for (int r0 = 0; r0 < nrows; r0 += 32) {
+        const int r = r0 + lane;
+        uint32_t s0 = 0u, n0 = 0u, s1 = 0u, n1 = 0u;
+        if (r < nrows) {
+            const int iz = b.iz0 + r / ny, iy = b.iy0 + r % ny;
+            int xa, xb;
+            row_xrange(Hj, G, b, rcu, true, iy, iz, xa, xb);
+            if (xa <= xb) {
+                const int ixe = min(xb, xa | (B - 1));
+                const uint32_t b0 = ppm_bucket(xa, iy, iz, G);
+                s0 = __ldg(a.cell_start + b0);
+                n0 = __ldg(a.cell_start + b0 + (uint32_t)(ixe - xa) + 1u) - s0;
+                if (ixe < xb) {
+                    const uint32_t b1 = ppm_bucket(ixe + 1, iy, iz, G);
+                    s1 = __ldg(a.cell_start + b1);
+                    n1 = __ldg(a.cell_start + b1 + (uint32_t)(xb - ixe - 1) + 1u) - s1;
+                }
+            }
+        }
+        const int k = (n0 > 0u ? 1 : 0) + (n1 > 0u ? 1 : 0);
+        int inc = k;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(full, inc, o);
+            if (lane >= o) inc += y;
+        }
+        int at = nruns + inc - k;
+        if (n0 > 0u) { wh.run_s[at] = s0; wh.run_n[at] = n0; ++at; }
+        if (n1 > 0u) { wh.run_s[at] = s1; wh.run_n[at] = n1; }
+        nruns += __shfl_sync(full, inc, 31);
+    }
+    __syncwarp();
+    Acc<NCH> la;                       // this lane's RGB flux sums of Hj
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) { la.phi[c] = 0.f; la.comp[c] = 0.f; la.part[c] = 0.f; }
+    int qn = 0;                        // queued pairs (warp-uniform)
+    for (int ri = 0; ri < nruns; ++ri) {
+        const uint32_t s = wh.run_s[ri], n = wh.run_n[ri];
+        if (lane == 0) acc.cand += n;
+        for (uint32_t k0 = 0; k0 < n; k0 += 32u) {
+            const uint32_t k = k0 + (uint32_t)lane;
+            float dx = 0.f, dy = 0.f, dz = 0.f;
+            float4 X = make_float4(0.f, 0.f, 0.f, 0.f);
+            bool in = false;
+            if (k < n) {
+                X = __ldg(a.rec0 + s + k);
+                in = in_disk(Hj, X, dx, dy, dz);
+            }
+            const unsigned bal = __ballot_sync(full, in);
+            if (in) {
+                const int at = qn + __popc(bal & lt);
+                wh.pd[at] = make_float4(dx, dy, dz, X.w);
+                wh.pp[at] = s + k;
+            }
+            qn += __popc(bal);
+            if (qn >= 32) {
+                __syncwarp();
+                const float4 D = wh.pd[lane];
+                const uint32_t p = wh.pp[lane];
+                float4 Dn = make_float4(0.f, 0.f, 0.f, 0.f);
+                uint32_t pn = 0u;
+                if (lane < qn - 32) { Dn = wh.pd[32 + lane]; pn = wh.pp[32 + lane]; }
+                __syncwarp();
+                if (lane < qn - 32) { wh.pd[lane] = Dn; wh.pp[lane] = pn; }
+                qn -= 32;
+                gather_pair<NCH, NTC, NORMALS, VCM, BATCH>(a, Hj, lp, tid, la, p, D, D.x, D.y, D.z);
+                flush_run<NCH, NTC>(la);
+                __syncwarp();
+            }
+        }
+    }
+    __syncwarp();
+    if (lane < qn) {
+        const float4 D = wh.pd[lane];
+        gather_pair<NCH, NTC, NORMALS, VCM, BATCH>(a, Hj, lp, tid, la, wh.pp[lane], D, D.x, D.y, D.z);
+    }
+    flush_run<NCH, NTC>(la);
+    __syncwarp();
+    // the lanes' columns -> the owner's slots (and cleared for the next hit point)
+#pragma unroll
+    for (int c = 0; c < NTC; ++c) {
+        float v[32];
+#pragma unroll
+        for (int g = 0; g < PPM_NG; ++g) {
+            const float2 q = lp.SQ[c][g][tid];
+            v[g] = q.x;
+            v[PPM_NG + g] = q.y;
+            lp.SQ[c][g][tid] = make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 2 * PPM_NG; i < 32; ++i) v[i] = 0.f;
+        const float t = warp_reduce_scatter<32>(v, lane);        // lane l: value l
+        if (lane < PPM_NG) sm.SQ[c][lane][owner].x = t;
+        else if (lane < 2 * PPM_NG) sm.SQ[c][lane - PPM_NG][owner].y = t;
+    }
+    uint32_t cc[16];
+#pragma unroll
+    for (int g = 0; g < PPM_NG; ++g) { cc[g] = lp.c[g][tid]; lp.c[g][tid] = 0u; }
+#pragma unroll
+    for (int i = PPM_NG; i < 16; ++i) cc[i] = 0u;
+    const uint32_t ct = warp_reduce_scatter<16>(cc, lane);    // lane l: count l / 2
+    if ((lane & 1) == 0 && (lane >> 1) < PPM_NG) sm.c[lane >> 1][owner] = ct;
+    if constexpr (NCH == 3 && NTC == 1) {
+        // the lanes' compensated RGB sums, added over the warp
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float f = la.phi[c] - la.comp[c];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(full, f, o);
+            if (lane == (owner & 31)) { acc.phi[c] = f; acc.comp[c] = 0.f; }
+        }
+    }
+    __syncwarp();
+}
+
 // FEAT: also write the proposer's features (a separate instantiation: the
 // call alone costs the feature-free kernel about 10% through register
 // allocation in the cell walk).  CHI2: CPPM's count test decides instead of
@@ -754,11 +942,12 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
 #pragma unroll
             for (int c = 0; c < NTC; ++c) sm.SQ[c][g][tid] = make_float2(0.f, 0.f);
         }
-        if constexpr (MAPPING == 4) {
+        if constexpr (MAPPING == 4 || MAPPING == 6) {
 #pragma unroll
             for (int g = 0; g < PPM_NG; ++g) {
                 bsh.lp.c[g][tid] = 0u;
-                bsh.lp.SQ[0][g][tid] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < NTC; ++c) bsh.lp.SQ[c][g][tid] = make_float2(0.f, 0.f);
             }
         }
     } else {
@@ -774,7 +963,7 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
 
     Acc<NCH> acc;
 #pragma unroll
-    for (int c = 0; c < NCH; ++c) { acc.phi[c] = 0.f; acc.comp[c] = 0.f; }
+    for (int c = 0; c < NCH; ++c) { acc.phi[c] = 0.f; acc.comp[c] = 0.f; acc.part[c] = 0.f; }
     Hit H;
     H.r = 0.f; H.r2 = 0.f;
     GridGeom G = *pr.geom;
@@ -808,6 +997,28 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
         __syncwarp();
         if (__any_sync(0xffffffffu, live))
             gather_lockstep<NCH, NTC, NORMALS, VCM, BATCH>(a, H, G, b, live, sm, bsh.lq, tid, lane, w, acc);
+    } else if constexpr (MAPPING == 6) {
+        __syncwarp();
+        for (int j = 0; j < 32; ++j) {
+            if (!__shfl_sync(0xffffffffu, (int)live, j)) continue;   // warp-uniform
+            Hit Hj;
+            Hj.P = shfl_f4(H.P, j);
+            Hj.U = shfl_f4(H.U, j);
+            Hj.V = shfl_f4(H.V, j);
+            Hj.r = __shfl_sync(0xffffffffu, H.r, j);
+            Hj.r2 = __shfl_sync(0xffffffffu, H.r2, j);
+            Hj.inv_eta = __shfl_sync(0xffffffffu, H.inv_eta, j);
+            Hj.nqh = __shfl_sync(0xffffffffu, H.nqh, j);
+            Hj.pid = H.pid;
+            CellBox bj;
+            bj.ix0 = __shfl_sync(0xffffffffu, b.ix0, j); bj.ix1 = __shfl_sync(0xffffffffu, b.ix1, j);
+            bj.iy0 = __shfl_sync(0xffffffffu, b.iy0, j); bj.iy1 = __shfl_sync(0xffffffffu, b.iy1, j);
+            bj.iz0 = __shfl_sync(0xffffffffu, b.iz0, j); bj.iz1 = __shfl_sync(0xffffffffu, b.iz1, j);
+            bj.rc = __shfl_sync(0xffffffffu, b.rc, j);
+            gather_warp_hit_compact<NCH, NTC, NORMALS, VCM, BATCH>(a, Hj, G, bj, bsh.lp, sm, bsh.wh[w], tid,
+                                                                   lane, w * 32 + j, acc);
+        }
+        __syncwarp();
     } else if constexpr (MAPPING == 4) {
         __syncwarp();
         for (int j = 0; j < 32; ++j) {
@@ -984,6 +1195,7 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
         }
     }
 
+    flush_run<NCH, NTC>(acc);       // a run's sums not yet flushed (fallback walks)
     // this iteration's sums of this thread's hit point
     const GroupSums<NCH, NTC, MAPPING> gs{bsh, tid, fs};
     if constexpr (MAPPING == 3) {

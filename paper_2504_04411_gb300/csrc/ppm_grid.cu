@@ -129,8 +129,11 @@ k_cell_start(const uint32_t* __restrict__ keys, int64_t n, uint32_t T,
 }
 
 // records of packed photon vals[i] (stride 1 + REC1 + AUX float4s) into
-// the gather's separate sorted arrays; nothing when the sort gave up (the
-// values are then no permutation of [0, n))
+// the gather's sorted arrays: rec0 on its own (every candidate reads it);
+// with both the other records, rec1 and aux side by side in rec1 (32 bytes
+// a photon, one sector for an in-disk pair), else each in its own array.
+// Nothing when the sort gave up (the values are then no permutation of
+// [0, n)).
 template <bool REC1, bool AUX>
 __global__ void __launch_bounds__(256)
 k_permute(int64_t n, const uint32_t* __restrict__ vals, const float4* __restrict__ pack,
@@ -142,8 +145,13 @@ k_permute(int64_t n, const uint32_t* __restrict__ vals, const float4* __restrict
     if (i >= n || (*err & 4)) return;
     const float4* src = pack + (int64_t)vals[i] * S;
     rec0[i] = __ldg(src);
-    if constexpr (REC1) rec1[i] = __ldg(src + 1);
-    if constexpr (AUX) aux[i] = __ldg(reinterpret_cast<const uint4*>(src) + (S - 1));
+    if constexpr (REC1 && AUX) {
+        rec1[2 * i] = __ldg(src + 1);
+        reinterpret_cast<uint4*>(rec1)[2 * i + 1] = __ldg(reinterpret_cast<const uint4*>(src) + 2);
+    } else {
+        if constexpr (REC1) rec1[i] = __ldg(src + 1);
+        if constexpr (AUX) aux[i] = __ldg(reinterpret_cast<const uint4*>(src) + (S - 1));
+    }
 }
 
 template <int NCH, bool AUX, bool VCM>
@@ -175,7 +183,7 @@ int reserve_photons(ppm_ctx* c, int64_t n)
     // whether the iteration brings normals)
     if (cudaMalloc(&c->pack, cap * (rec1 ? 3 : 2) * sizeof(float4)) != cudaSuccess ||
         cudaMalloc(&c->rec0, cap * sizeof(float4)) != cudaSuccess ||
-        (rec1 && cudaMalloc(&c->rec1, cap * sizeof(float4)) != cudaSuccess) ||
+        (rec1 && cudaMalloc(&c->rec1, 2 * cap * sizeof(float4)) != cudaSuccess) ||   // rec1 | aux side by side
         cudaMalloc(&c->aux, cap * sizeof(uint4)) != cudaSuccess) {
         cudaGetLastError();
         return PPM_ENOMEM;
@@ -208,7 +216,8 @@ int ppm_grid_build(ppm_ctx* c, const ppm_photons* ph)
     if (rc) return rc;
     // hash blocks of 4^3 cells suffice for one sphere (<= 4 cells per axis at
     // cell_factor >= 1); the warp-union traversal and cell_factor < 1 need 8^3
-    const int lb = (c->prm.cell_factor >= 1.0f && (c->prm.mapping == 0 || c->prm.mapping == 5)) ? 2 : 3;   // union traversals: 8^3
+    const int m = c->prm.mapping;
+    const int lb = (c->prm.cell_factor >= 1.0f && (m == 0 || m == 5 || m == 6)) ? 2 : 3;   // union traversals: 8^3
     c->tbits = ppm_table_bits(n, lb);
     const uint32_t T = 1u << c->tbits;
     if ((int64_t)T + 1 > c->cs_cap) {

@@ -126,6 +126,27 @@ def train(X, Y, M, epochs: int = 20, batch: int = 4096, lr: float = 2e-3, seed: 
     return blob, master, losses
 
 
+# (doom threshold, smallest shrink ratio) settings the validation chooses from
+SETTINGS = ((0.5, 0.1), (0.7, 0.25), (0.85, 0.5), (0.95, 0.5), (0.99, 0.7))
+
+
+def select(blob, scene, iters: int, reference, params=None, settings=SETTINGS):
+    """Choose the proposer's setting on a validation scene (a seed that is
+    neither the training nor the test seed): the setting with the lowest
+    radiance MSE after `iters` iterations, or None -- the proposer off --
+    when none beats the plain method there.  Returns (setting, {setting or
+    "plain": MSE})."""
+    mses = {"plain": run(scene, iters, params=params, reference=reference, collect=False).mse[-1]}
+    best, best_mse = None, mses["plain"]
+    for thr, mr in settings:
+        m = run(scene, iters, params=params, blob=blob, threshold=thr, min_ratio=mr, reference=reference,
+                collect=False).mse[-1]
+        mses[f"{thr},{mr}"] = m
+        if m < best_mse:
+            best, best_mse = (thr, mr), m
+    return best, mses
+
+
 def iterations_to_reach(mse: list, target: float) -> int | None:
     for i, v in enumerate(mse):
         if v <= target:
