@@ -207,6 +207,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--shrink", type=int, default=1,
+                    help="profiling cases only: hit points and photons / N, r0 x sqrt(N) (vcm, frame)")
     a = ap.parse_args()
     if a.steps is None:
         a.steps = 16 if a.config in ("batched", "vcm") else (64 if a.config in ("learned", "learned_frame", "cppm",
@@ -215,7 +217,21 @@ def parse():
     return a
 
 
-def make_scene(config, rank):
+def make_scene(config, rank, shrink=1):
+    """The workload's scene; shrink > 1 (profiling only) divides the hit
+    points and photons by shrink and widens r0 by sqrt(shrink), so a disk
+    holds as many photons as at full size."""
+    sc, desc = _make_scene(config, rank)
+    if shrink > 1 and config in ("vcm", "frame"):
+        import dataclasses as dc
+        import math
+        sc = dc.replace(sc, nh=sc.nh // shrink, J=sc.J // shrink, r0=sc.r0 * math.sqrt(shrink))
+        desc = dict(desc, workload=f"profiling case: {desc['workload']} with hit points and photons / {shrink}, "
+                                   f"r0 x sqrt({shrink})", hit_points=sc.nh, photons_per_iter=sc.J, r0=sc.r0)
+    return sc, desc
+
+
+def _make_scene(config, rank):
     from paper_2504_04411_gb300 import synth
     if config == "tiny":
         sc = synth.PlaneScene(nside=64, J=100_000, r0=0.02, step=True, seed=synth.SEED_BASE + 1000 * rank)
@@ -323,7 +339,7 @@ def run_single(args, rank, world, local, dist):
     import torch
 
     from paper_2504_04411_gb300 import autotune, ppm, synth
-    sc, desc = make_scene(args.config, rank)
+    sc, desc = make_scene(args.config, rank, args.shrink)
     W, K = args.warmup, args.steps
     hp = sc.hitpoints("cuda")
     batches = [sc.photons(i, "cuda") for i in range(1, W + K + 1)]

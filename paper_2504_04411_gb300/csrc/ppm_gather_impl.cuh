@@ -79,10 +79,10 @@ struct Prob {
 // coefficient of variation of the group sums, max_g c_g/C.
 constexpr int kFeatures = 12;
 
-template <int NTC>
+template <int NTC, int SLOTS = kThreads>
 struct Smem {
-    uint32_t c[PPM_NG][kThreads];
-    float2 SQ[NTC][PPM_NG][kThreads];   // (sum psi, sum psi^2)
+    uint32_t c[PPM_NG][SLOTS];
+    float2 SQ[NTC][PPM_NG][SLOTS];      // (sum psi, sum psi^2)
 };
 
 template <int QCAP>
@@ -190,8 +190,8 @@ __device__ __forceinline__ bool in_disk(const Hit& H, const float4& X, float& dx
 }
 
 // everything after the disk test for photon p (record X)
-template <int NCH, int NTC, bool NORMALS, bool VCM, bool BATCH>
-__device__ __forceinline__ void gather_pair(const GatherArgs& a, const Hit& H, Smem<NTC>& sm, int tid,
+template <int NCH, int NTC, bool NORMALS, bool VCM, bool BATCH, typename SM>
+__device__ __forceinline__ void gather_pair(const GatherArgs& a, const Hit& H, SM& sm, int tid,
                                             Acc<NCH>& acc, uint32_t p, const float4& X,
                                             float dx, float dy, float dz)
 {
@@ -310,9 +310,9 @@ __device__ __forceinline__ void row_xrange(const Hit& H, const GridGeom& G, cons
 }
 
 // traversal 0: the thread walks its own cells
-template <int NCH, int NTC, bool NORMALS, bool VCM, bool BATCH>
+template <int NCH, int NTC, bool NORMALS, bool VCM, bool BATCH, typename SM>
 __device__ void gather_own(const GatherArgs& a, const Hit& H, const GridGeom& G, CellBox b,
-                           Smem<NTC>& sm, int tid, Acc<NCH>& acc)
+                           SM& sm, int tid, Acc<NCH>& acc)
 {
     const int B = 1 << G.lb;
     if (b.ix1 - b.ix0 >= B || b.iy1 - b.iy0 >= B || b.iz1 - b.iz0 >= B) {
@@ -519,7 +519,8 @@ struct FixSmem {
 
 template <int NCH, int NTC, int MAPPING>
 struct BlockShared {
-    typename std::conditional<MAPPING == 3, Empty, Smem<NTC>>::type sm;
+    typename std::conditional<MAPPING == 3, Empty,
+                              typename std::conditional<MAPPING == 7, Smem<NTC, 2 * kThreads>, Smem<NTC>>::type>::type sm;
     typename std::conditional<MAPPING == 5, LockQueue, Empty>::type lq;
     typename std::conditional<MAPPING == 1 || MAPPING == 2, UnionSmem<MAPPING == 2 ? 64 : 32>, Empty>::type us;
     typename std::conditional<MAPPING == 3, PairSmem, Empty>::type ps;
@@ -644,9 +645,9 @@ __device__ __forceinline__ void drain_pairs(const GatherArgs& a, PairSmem& ps, F
 
 // the 12 features of the learned proposer for hit point h (out of line:
 // only contexts with features enabled pay for its registers)
-template <int NCH, int NTC, int MAPPING>
+template <int NCH, int NTC, typename GS>
 __device__ __noinline__ void write_features(const GatherArgs& a, const Prob& pr,
-                                            const GroupSums<NCH, NTC, MAPPING>& gs, int64_t h,
+                                            const GS& gs, int64_t h,
                                             const float* Sg, float Ssum, float dev2, float F, float fc,
                                             float r, int32_t tp)
 {
@@ -673,9 +674,117 @@ __device__ __noinline__ void write_features(const GatherArgs& a, const Prob& pr,
     for (int q = 0; q < kFeatures; ++q) a.feat[(int64_t)q * nh + h] = f[q];
 }
 
-// The hit points [h0, h_end) (at most one block's worth, h0 + tid for this
-// thread) of problem pr: gather, test, update; block-wide reductions into
-// pr's counters.  Ends with a block barrier, so it can be called in a loop.
+// Eq. f-statistic, the test, Eq. radiusupdate and the estimate of
+// Eq. progressive-VCM-estimator for hit point h (radius r) from this
+// iteration's sums gs (S(c, g), Q(c, g), C(g)) and the stored window; the
+// new radius, the rejection and the pair count are returned for the
+// block's reductions
+template <int NCH, int NTC, bool FEAT, bool CHI2, typename GS>
+__device__ __forceinline__ void update_hit(const GatherArgs& a, const Prob& pr, const GS& gs, int64_t h, float r,
+                                           Acc<NCH>& acc, float& r_new, unsigned long long& rej,
+                                           unsigned long long& pairs)
+{
+    const int32_t tp = a.t[h] + 1;
+    // a window longer than the table can only come from ppm_set_state
+    // with t >= the iteration count: clamp the lookup and flag it
+    int32_t tpi = tp;
+    if (tp < 1 || tp > pr.fc_max) { atomicOr(a.err, 2); tpi = max(1, min(tp, pr.fc_max)); }
+    // m = t' J samples per group never exists in FP32: the table holds
+    // 1/m and 12 (m-1) / (11 m), each computed in FP64 and rounded once
+    const float2 mf = pr.fm[tpi];
+    const int64_t nh = a.nh;
+    bool reject = false;
+    float F0 = 0.f;
+    // CPPM (Sec. 3.2.3): Pearson's X^2 of the window's in-disk counts
+    // against an even spread, from exact integers:
+    // X^2 = (12 sum_g c_g^2 - C^2) / C, C = sum_g c_g (0 without photons)
+    double x2 = 0.0;
+    if constexpr (CHI2) {
+        unsigned long long C = 0ull, C2 = 0ull;
+#pragma unroll
+        for (int g = 0; g < PPM_NG; ++g) {
+            const unsigned long long cg = (unsigned long long)a.cnt[g * nh + h] + gs.C(g);
+            C += cg;
+            C2 += cg * cg;
+        }
+        if (C > 0ull) x2 = (double)(PPM_NG * C2 - C * C) / (double)C;
+        reject = x2 > pr.fc[tpi];
+    }
+#pragma unroll
+    for (int c = 0; c < NTC; ++c) {
+        float Sg[PPM_NG];
+        float Ssum = 0.f, Qsum = 0.f, S2 = 0.f;
+#pragma unroll
+        for (int g = 0; g < PPM_NG; ++g) {
+            const int64_t o = ((int64_t)c * PPM_NG + g) * nh + h;
+            Sg[g] = a.S[o] + gs.S(c, g);
+            Qsum += a.Q[o] + gs.Q(c, g);
+            Ssum += Sg[g];
+            S2 = fmaf(Sg[g], Sg[g], S2);
+        }
+        const float Sbar = Ssum * (1.0f / PPM_NG);
+        float dev2 = 0.f;
+#pragma unroll
+        for (int g = 0; g < PPM_NG; ++g) { const float d = Sg[g] - Sbar; dev2 = fmaf(d, d, dev2); }
+        // SSB = dev2 / m, SSW = sum Q - sum S^2 / m,
+        // F = (SSB / 11) / (SSW / (12 (m-1))) = (dev2 / SSW) * 12 (m-1) / (11 m)
+        const float ssw = Qsum - S2 * mf.x;
+        float F = 0.f;
+        if (ssw > 0.f) F = (dev2 / ssw) * mf.y;
+        if (c == 0) F0 = CHI2 ? (float)x2 : F;
+        if (!CHI2 && ssw > 0.f && (double)F > pr.fc[tpi]) reject = true;
+        if constexpr (FEAT)
+            if (c == 0) write_features<NCH, NTC>(a, pr, gs, h, Sg, Ssum, dev2, F, (float)pr.fc[tpi], r, tp);
+    }
+    // Eq. (progressive-VCM-estimator): kernel estimate with this r_i;
+    // Phi_i = sum over groups of this iteration's psi sums unless RGB
+    // flux is tested on its luminance
+    if constexpr (!(NCH == 3 && NTC == 1)) {
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            float f = 0.f;
+#pragma unroll
+            for (int g = 0; g < PPM_NG; ++g) f += gs.S(c, g);
+            acc.phi[c] = f;
+        }
+    }
+    const float inv_area = __frcp_rn(__fmul_rn(3.14159265358979f, __fmul_rn(r, r)));
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) a.tau[h * NCH + c] += (double)__fmul_rn(acc.phi[c], inv_area);
+#pragma unroll
+    for (int g = 0; g < PPM_NG; ++g) pairs += gs.C(g);
+    a.F[h] = F0;
+    if (reject) {
+        r_new = fmaxf(__fmul_rn(pr.k, r), pr.bound);
+        a.r[h] = r_new;
+        a.t[h] = 0;
+#pragma unroll
+        for (int g = 0; g < PPM_NG; ++g) a.cnt[g * nh + h] = 0u;
+#pragma unroll
+        for (int c = 0; c < NTC; ++c)
+#pragma unroll
+            for (int g = 0; g < PPM_NG; ++g) {
+                const int64_t o = ((int64_t)c * PPM_NG + g) * nh + h;
+                a.S[o] = 0.f;
+                a.Q[o] = 0.f;
+            }
+        rej = 1;
+    } else {
+        r_new = r;
+        a.t[h] = tp;
+#pragma unroll
+        for (int g = 0; g < PPM_NG; ++g) a.cnt[g * nh + h] += gs.C(g);
+#pragma unroll
+        for (int c = 0; c < NTC; ++c)
+#pragma unroll
+            for (int g = 0; g < PPM_NG; ++g) {
+                const int64_t o = ((int64_t)c * PPM_NG + g) * nh + h;
+                a.S[o] += gs.S(c, g);
+                a.Q[o] += gs.Q(c, g);
+            }
+    }
+}
+
 // Reduce-scatter of N values (N a power of two, <= 32) over the warp by
 // recursive halving: at each step a lane keeps half of its values, adds its
 // partner's copy of that half and passes on the other half.  Returns, on
@@ -919,6 +1028,9 @@ __device__ __forceinline__ void gather_warp_hit_compact(const GatherArgs& a, con
     __syncwarp();
 }
 
+// The hit points [h0, h_end) (at most one block's worth, h0 + tid for this
+// thread) of problem pr: gather, test, update; block-wide reductions into
+// pr's counters.  Ends with a block barrier, so it can be called in a loop.
 // FEAT: also write the proposer's features (a separate instantiation: the
 // call alone costs the feature-free kernel about 10% through register
 // allocation in the cell walk).  CHI2: CPPM's count test decides instead of
@@ -1209,108 +1321,7 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
     // ---------------- epilogue: F-test, estimate, radius update ----------
     float r_new = 0.f;
     unsigned long long rej = 0, pairs = 0;
-    if (live) {
-        const float r = H.r;
-        const int32_t tp = a.t[h] + 1;
-        // a window longer than the table can only come from ppm_set_state
-        // with t >= the iteration count: clamp the lookup and flag it
-        int32_t tpi = tp;
-        if (tp < 1 || tp > pr.fc_max) { atomicOr(a.err, 2); tpi = max(1, min(tp, pr.fc_max)); }
-        // m = t' J samples per group never exists in FP32: the table holds
-        // 1/m and 12 (m-1) / (11 m), each computed in FP64 and rounded once
-        const float2 mf = pr.fm[tpi];
-        const int64_t nh = a.nh;
-        bool reject = false;
-        float F0 = 0.f;
-        // CPPM (Sec. 3.2.3): Pearson's X^2 of the window's in-disk counts
-        // against an even spread, from exact integers:
-        // X^2 = (12 sum_g c_g^2 - C^2) / C, C = sum_g c_g (0 without photons)
-        double x2 = 0.0;
-        if constexpr (CHI2) {
-            unsigned long long C = 0ull, C2 = 0ull;
-#pragma unroll
-            for (int g = 0; g < PPM_NG; ++g) {
-                const unsigned long long cg = (unsigned long long)a.cnt[g * nh + h] + gs.C(g);
-                C += cg;
-                C2 += cg * cg;
-            }
-            if (C > 0ull) x2 = (double)(PPM_NG * C2 - C * C) / (double)C;
-            reject = x2 > pr.fc[tpi];
-        }
-#pragma unroll
-        for (int c = 0; c < NTC; ++c) {
-            float Sg[PPM_NG];
-            float Ssum = 0.f, Qsum = 0.f, S2 = 0.f;
-#pragma unroll
-            for (int g = 0; g < PPM_NG; ++g) {
-                const int64_t o = ((int64_t)c * PPM_NG + g) * nh + h;
-                Sg[g] = a.S[o] + gs.S(c, g);
-                Qsum += a.Q[o] + gs.Q(c, g);
-                Ssum += Sg[g];
-                S2 = fmaf(Sg[g], Sg[g], S2);
-            }
-            const float Sbar = Ssum * (1.0f / PPM_NG);
-            float dev2 = 0.f;
-#pragma unroll
-            for (int g = 0; g < PPM_NG; ++g) { const float d = Sg[g] - Sbar; dev2 = fmaf(d, d, dev2); }
-            // SSB = dev2 / m, SSW = sum Q - sum S^2 / m,
-            // F = (SSB / 11) / (SSW / (12 (m-1))) = (dev2 / SSW) * 12 (m-1) / (11 m)
-            const float ssw = Qsum - S2 * mf.x;
-            float F = 0.f;
-            if (ssw > 0.f) F = (dev2 / ssw) * mf.y;
-            if (c == 0) F0 = CHI2 ? (float)x2 : F;
-            if (!CHI2 && ssw > 0.f && (double)F > pr.fc[tpi]) reject = true;
-            if constexpr (FEAT)
-                if (c == 0) write_features<NCH, NTC, MAPPING>(a, pr, gs, h, Sg, Ssum, dev2, F, (float)pr.fc[tpi], r, tp);
-        }
-        // Eq. (progressive-VCM-estimator): kernel estimate with this r_i;
-        // Phi_i = sum over groups of this iteration's psi sums unless RGB
-        // flux is tested on its luminance
-        if constexpr (!(NCH == 3 && NTC == 1)) {
-#pragma unroll
-            for (int c = 0; c < NCH; ++c) {
-                float f = 0.f;
-#pragma unroll
-                for (int g = 0; g < PPM_NG; ++g) f += gs.S(c, g);
-                acc.phi[c] = f;
-            }
-        }
-        const float inv_area = __frcp_rn(__fmul_rn(3.14159265358979f, __fmul_rn(r, r)));
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) a.tau[h * NCH + c] += (double)__fmul_rn(acc.phi[c], inv_area);
-#pragma unroll
-        for (int g = 0; g < PPM_NG; ++g) pairs += gs.C(g);
-        a.F[h] = F0;
-        if (reject) {
-            r_new = fmaxf(__fmul_rn(pr.k, r), pr.bound);
-            a.r[h] = r_new;
-            a.t[h] = 0;
-#pragma unroll
-            for (int g = 0; g < PPM_NG; ++g) a.cnt[g * nh + h] = 0u;
-#pragma unroll
-            for (int c = 0; c < NTC; ++c)
-#pragma unroll
-                for (int g = 0; g < PPM_NG; ++g) {
-                    const int64_t o = ((int64_t)c * PPM_NG + g) * nh + h;
-                    a.S[o] = 0.f;
-                    a.Q[o] = 0.f;
-                }
-            rej = 1;
-        } else {
-            r_new = r;
-            a.t[h] = tp;
-#pragma unroll
-            for (int g = 0; g < PPM_NG; ++g) a.cnt[g * nh + h] += gs.C(g);
-#pragma unroll
-            for (int c = 0; c < NTC; ++c)
-#pragma unroll
-                for (int g = 0; g < PPM_NG; ++g) {
-                    const int64_t o = ((int64_t)c * PPM_NG + g) * nh + h;
-                    a.S[o] += gs.S(c, g);
-                    a.Q[o] += gs.Q(c, g);
-                }
-        }
-    }
+    if (live) update_hit<NCH, NTC, FEAT, CHI2>(a, pr, gs, h, H.r, acc, r_new, rej, pairs);
 
     // block reductions: max radius for the next grid, counters
     __shared__ float s_rmax[kWarps];
@@ -1339,6 +1350,190 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
     __syncthreads();
 }
 
+// this iteration's sums of slot `slot` of a block's slots (traversal 7)
+template <int NTC, int SLOTS>
+struct SlotSums {
+    const Smem<NTC, SLOTS>& sm;
+    int slot;
+    __device__ __forceinline__ float S(int c, int g) const { return sm.SQ[c][g][slot].x; }
+    __device__ __forceinline__ float Q(int c, int g) const { return sm.SQ[c][g][slot].y; }
+    __device__ __forceinline__ uint32_t C(int g) const { return sm.c[g][slot]; }
+};
+
+// one hit point of traversal 7: loaded, its cull box, or a dead slot
+__device__ __forceinline__ void load_hit(const GatherArgs& a, const Prob& pr, const GridGeom& G, int64_t h,
+                                         bool live, uint32_t pid, Hit& H, CellBox& b)
+{
+    H.pid = pid;
+    H.inv_eta = 0.f;
+    if (live) {
+        H.P = a.hp_pos[h];
+        H.U = a.hp_u[h];
+        H.V = a.hp_v[h];
+        H.r = a.r[h];
+        H.r2 = __fmul_rn(H.r, H.r);
+        H.nqh = __float_as_uint(H.P.w);
+        b = cell_box(H, G);
+    } else {
+        H.P = make_float4(0.f, 0.f, 0.f, 0.f);
+        H.U = H.V = H.P;
+        H.nqh = 0u;
+        H.r = 0.f;
+        H.r2 = -1.f;                      // no photon passes d2 <= -1
+        b = CellBox{INT_MAX, INT_MIN, INT_MAX, INT_MIN, INT_MAX, INT_MIN, 0.f};
+    }
+}
+
+// Traversal 7: two neighbouring hit points a thread (slots 2 tid and
+// 2 tid + 1 of the block's 2 kThreads; consecutive along the Hilbert curve,
+// so their disks overlap almost entirely).  The thread walks the cells of
+// both boxes once -- rows trimmed to a sphere that holds both cull spheres
+// -- and tests every photon it loads against both disks, so a record load
+// and the loop around it serve two tests.  Each hit point's in-disk photons
+// are classified in the order of traversal 0's walk (the walk covers its
+// own trimmed rows in the same order), so the group sums are bit-identical
+// to traversal 0's (the RGB flux sums of a luminance test split into runs
+// differently).  A pair whose joint box spans more than a hash block walks
+// each hit point on its own.
+template <int NCH, int NTC, bool NORMALS, bool VCM, bool BATCH>
+__device__ __forceinline__ void gather_block_pair(const GatherArgs& a, const Prob& pr, int64_t h0, int64_t h_end,
+                                                  BlockShared<NCH, NTC, 7>& bsh)
+{
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    auto& sm = bsh.sm;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int slot = 2 * tid + k;
+#pragma unroll
+        for (int g = 0; g < PPM_NG; ++g) {
+            sm.c[g][slot] = 0u;
+#pragma unroll
+            for (int c = 0; c < NTC; ++c) sm.SQ[c][g][slot] = make_float2(0.f, 0.f);
+        }
+    }
+    GridGeom G = *pr.geom;
+    if constexpr (!BATCH) G.pid = 0u;
+    const uint32_t pid = BATCH ? pr.pid : 0u;
+    const int64_t ha = h0 + 2 * tid, hb = ha + 1;
+    const bool la = ha < h_end, lb = hb < h_end;
+    Hit A, Bh;
+    CellBox ba, bb;
+    load_hit(a, pr, G, ha, la, pid, A, ba);
+    load_hit(a, pr, G, hb, lb, pid, Bh, bb);
+    if constexpr (VCM) {
+        if (la) A.inv_eta = __frcp_rn(__fmul_rn(__fmul_rn(pr.n_vm, 3.14159265358979f), A.r2));
+        if (lb) Bh.inv_eta = __frcp_rn(__fmul_rn(__fmul_rn(pr.n_vm, 3.14159265358979f), Bh.r2));
+    }
+    Acc<NCH> acc_a, acc_b;
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        acc_a.phi[c] = acc_a.comp[c] = acc_a.part[c] = 0.f;
+        acc_b.phi[c] = acc_b.comp[c] = acc_b.part[c] = 0.f;
+    }
+    const int Bk = 1 << G.lb;
+    const int sa = 2 * tid, sb = 2 * tid + 1;
+    // the joint box, or each hit point on its own
+    CellBox bj{min(ba.ix0, bb.ix0), max(ba.ix1, bb.ix1), min(ba.iy0, bb.iy0), max(ba.iy1, bb.iy1),
+               min(ba.iz0, bb.iz0), max(ba.iz1, bb.iz1), 0.f};
+    const bool joint = la && lb && bj.ix1 - bj.ix0 < Bk && bj.iy1 - bj.iy0 < Bk && bj.iz1 - bj.iz0 < Bk;
+    if (!joint) {
+        if (la) gather_own<NCH, NTC, NORMALS, VCM, BATCH>(a, A, G, ba, sm, sa, acc_a);
+        if (lb) gather_own<NCH, NTC, NORMALS, VCM, BATCH>(a, Bh, G, bb, sm, sb, acc_b);
+    } else {
+        // a sphere holding both cull spheres: centre at the midpoint, radius
+        // the larger cull radius plus half the distance (rounded up)
+        Hit M = A;
+        M.P.x = 0.5f * (A.P.x + Bh.P.x);
+        M.P.y = 0.5f * (A.P.y + Bh.P.y);
+        M.P.z = 0.5f * (A.P.z + Bh.P.z);
+        const float ddx = A.P.x - Bh.P.x, ddy = A.P.y - Bh.P.y, ddz = A.P.z - Bh.P.z;
+        const float half = 0.5f * sqrtf(fmaf(ddz, ddz, fmaf(ddy, ddy, ddx * ddx)));
+        bj.rc = fmaxf(ba.rc, bb.rc) + half * 1.0009765625f + (fabsf(M.P.x) + fabsf(M.P.y) + fabsf(M.P.z)) * 1.0e-6f;
+        const RowCull rcu = row_cull(M, G, bj);
+        for (int iz = bj.iz0; iz <= bj.iz1; ++iz) {
+            const float gz = slab_gap(M.P.z, iz, G, rcu.eps);
+            const float rz2 = rcu.rc2 - gz * gz;
+            if (rz2 + rcu.slack < 0.f) continue;
+            for (int iy = bj.iy0; iy <= bj.iy1; ++iy) {
+                const float gy = slab_gap(M.P.y, iy, G, rcu.eps);
+                const float ryz2 = rz2 - gy * gy;
+                if (ryz2 + rcu.slack < 0.f) continue;
+                const float hw = sqrtf(fmaxf(ryz2, 0.f) + rcu.slack) + rcu.eps;
+                const int xa = max(bj.ix0, ppm_cell_coord(__fsub_rn(M.P.x, hw), G.inv_h));
+                const int xb = min(bj.ix1, ppm_cell_coord(__fadd_rn(M.P.x, hw), G.inv_h));
+                int ix = xa;
+                while (ix <= xb) {
+                    const int ixe = min(xb, ix | (Bk - 1));
+                    const uint32_t b0 = ppm_bucket(ix, iy, iz, G);
+                    const uint32_t s = __ldg(a.cell_start + b0);
+                    const uint32_t e = __ldg(a.cell_start + b0 + (uint32_t)(ixe - ix) + 1u);
+                    acc_a.cand += e - s;
+                    float4 Xn = s < e ? __ldg(a.rec0 + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (uint32_t p = s; p < e; ++p) {
+                        const float4 X = Xn;
+                        if (p + 1u < e) Xn = __ldg(a.rec0 + p + 1u);
+                        float dx, dy, dz;
+                        if (in_disk(A, X, dx, dy, dz))
+                            gather_pair<NCH, NTC, NORMALS, VCM, BATCH>(a, A, sm, sa, acc_a, p, X, dx, dy, dz);
+                        if (in_disk(Bh, X, dx, dy, dz))
+                            gather_pair<NCH, NTC, NORMALS, VCM, BATCH>(a, Bh, sm, sb, acc_b, p, X, dx, dy, dz);
+                    }
+                    if (e > s) { flush_run<NCH, NTC>(acc_a); flush_run<NCH, NTC>(acc_b); }
+                    ix = ixe + 1;
+                }
+            }
+        }
+    }
+    flush_run<NCH, NTC>(acc_a);
+    flush_run<NCH, NTC>(acc_b);
+
+    float r_new = 0.f, r_nb = 0.f;
+    unsigned long long rej = 0, pairs = 0;
+    if (la) update_hit<NCH, NTC, false, false>(a, pr, SlotSums<NTC, 2 * kThreads>{sm, sa}, ha, A.r, acc_a, r_new,
+                                               rej, pairs);
+    if (lb) update_hit<NCH, NTC, false, false>(a, pr, SlotSums<NTC, 2 * kThreads>{sm, sb}, hb, Bh.r, acc_b, r_nb,
+                                               rej, pairs);
+    r_new = fmaxf(r_new, r_nb);
+
+    __shared__ float s_rmax[kWarps];
+    __shared__ unsigned long long s_cnt3[3][kWarps];
+    const float wm = warp_max(r_new);
+    const unsigned long long wp = warp_sum_u64(pairs), wc = warp_sum_u64(acc_a.cand + acc_b.cand),
+                             wr = warp_sum_u64(rej);
+    if (lane == 0) {
+        s_rmax[w] = wm;
+        s_cnt3[0][w] = wp; s_cnt3[1][w] = wc; s_cnt3[2][w] = wr;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float m = 0.f;
+        unsigned long long pp = 0, c = 0, j = 0;
+#pragma unroll
+        for (int ww = 0; ww < kWarps; ++ww) {
+            m = fmaxf(m, s_rmax[ww]); pp += s_cnt3[0][ww]; c += s_cnt3[1][ww]; j += s_cnt3[2][ww];
+        }
+        atomicMax((int*)pr.rmax_next, __float_as_int(m));
+        atomicAdd(pr.counters + 0, pp);
+        atomicAdd(pr.counters + 1, c);
+        atomicAdd(pr.counters + 2, j);
+        atomicAdd(pr.counters + 3, pp);
+    }
+    __syncthreads();
+}
+
+// hit points [h0, h_end) of a block with the traversal's hit points per block
+template <int NCH, int NTC, bool NORMALS, bool VCM, int MAPPING, bool BATCH, bool FEAT = false, bool CHI2 = false>
+__device__ __forceinline__ void gather_any_block(const GatherArgs& a, const Prob& pr, int64_t h0, int64_t h_end,
+                                                 BlockShared<NCH, NTC, MAPPING>& bsh)
+{
+    if constexpr (MAPPING == 7) gather_block_pair<NCH, NTC, NORMALS, VCM, BATCH>(a, pr, h0, h_end, bsh);
+    else gather_block<NCH, NTC, NORMALS, VCM, MAPPING, BATCH, FEAT, CHI2>(a, pr, h0, h_end, bsh);
+}
+
+// hit points a block handles
+template <int MAPPING>
+constexpr int kHitsPerBlock = MAPPING == 7 ? 2 * kThreads : kThreads;
+
 // one context: one block per kThreads hit points
 template <int NCH, int NTC, bool NORMALS, bool VCM, int MAPPING, bool FEAT = false, bool CHI2 = false>
 __global__ void __launch_bounds__(kThreads, kMinBlocks<MAPPING, NTC>)
@@ -1346,8 +1541,8 @@ k_gather_update(GatherArgs a, Prob pr)
 {
     __shared__ BlockShared<NCH, NTC, MAPPING> bsh;
     if (*a.err & 4) return;          // the grid's sort gave up: no usable grid
-    const int64_t h0 = (int64_t)blockIdx.x * kThreads;
-    gather_block<NCH, NTC, NORMALS, VCM, MAPPING, false, FEAT, CHI2>(a, pr, h0, a.nh, bsh);
+    const int64_t h0 = (int64_t)blockIdx.x * kHitsPerBlock<MAPPING>;
+    gather_any_block<NCH, NTC, NORMALS, VCM, MAPPING, false, FEAT, CHI2>(a, pr, h0, a.nh, bsh);
 }
 
 }  // namespace

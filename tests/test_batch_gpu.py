@@ -51,7 +51,7 @@ def _run_batch(scenes, iters, params, cfs=None):
     return hps, phs, states, stats, L, graph
 
 
-@pytest.mark.parametrize("mapping", [0, 1, 3, 4, 5, 6])
+@pytest.mark.parametrize("mapping", [0, 1, 3, 4, 5, 6, 7])
 def test_batch_matches_oracle_per_problem(mapping):
     scenes = _problems()
     iters = 4
@@ -65,7 +65,7 @@ def test_batch_matches_oracle_per_problem(mapping):
         assert rep.diverged <= 2
 
 
-@pytest.mark.parametrize("mapping", [0, 1, 3, 4, 5, 6])
+@pytest.mark.parametrize("mapping", [0, 1, 3, 4, 5, 6, 7])
 def test_batch_bit_identical_to_single_contexts(mapping):
     """Traversals 0-3 and 5 visit a hit point's photons in the same order in
     a batch as in a context, so the state is bit-identical.  Traversals 4 and
@@ -179,7 +179,7 @@ def test_batch_windows_beyond_the_initial_critical_value_table():
 
 
 @pytest.mark.parametrize("mode", ["rgb", "rgb_test", "vcm_rgb", "vcm"])
-@pytest.mark.parametrize("mapping", [0, 1, 3, 4, 5, 6])
+@pytest.mark.parametrize("mapping", [0, 1, 3, 4, 5, 6, 7])
 def test_batch_rgb_and_vcm_problems_match_oracle(mode, mapping):
     """Batches of RGB problems (luminance test or one test per channel) and
     VCM+ problems (merge weights; RGB or one channel): every problem against
