@@ -110,12 +110,9 @@ typedef struct {
                            fixed-point group sums (one tested channel:
                            PPM_EINVAL with rgb_test), 4 = a warp per hit point
                            with shuffle-reduced group sums (one flux channel:
-                           PPM_EINVAL with channels = 3), 5 = each thread
-                           its own cells as 0, the warp's rows walked in
-                           step and the in-disk photons classified in step
-                           from per-lane queues (results bit-identical to 0).
-                           The features of the learned proposer and CPPM's
-                           count test always run traversal 0. */
+                           PPM_EINVAL with channels = 3).  The features of
+                           the learned proposer and CPPM's count test always
+                           run traversal 0. */
     int32_t tile;       /* batches: hit points per tile of the persistent
                            gather, a multiple of 64 in [64, 1024]; 0 = 64.
                            Contexts ignore it.  Results do not depend on it. */

@@ -320,7 +320,7 @@ int ppm_create(const ppm_hitpoints* hp, float r0, float alpha, const ppm_params*
     if (prm.rgb_test && prm.channels != 3) return PPM_EINVAL;
     if (prm.vcm && hp->n > 0 && (!hp->rho || !hp->nq)) return PPM_EINVAL;
     if (prm.n_vm < 0.f) return PPM_EINVAL;
-    if (prm.mapping < 0 || prm.mapping > 7) return PPM_EINVAL;
+    if (prm.mapping < 0 || prm.mapping > 4) return PPM_EINVAL;
     // traversal 3 tests one channel, traversal 4 gathers one flux channel
     if ((prm.mapping == 3 && prm.rgb_test) || (prm.mapping == 4 && prm.channels == 3)) return PPM_EINVAL;
     if (prm.test != 0 && prm.test != 1) return PPM_EINVAL;

@@ -290,8 +290,8 @@ k_batch_gather(GatherArgs a, BatchArgs bt)
         pr.inv_r0 = 0.f;
         pr.log_iter = 0.f;
         // a tile is one or more blocks' worth of hit points, done in turn
-        for (int64_t h0 = T.y; h0 < T.z; h0 += kHitsPerBlock<MAPPING>)
-            gather_any_block<NCH, NTC, NORMALS, VCM, MAPPING, true>(a, pr, h0, T.z, bsh);
+        for (int64_t h0 = T.y; h0 < T.z; h0 += kThreads)
+            gather_block<NCH, NTC, NORMALS, VCM, MAPPING, true>(a, pr, h0, T.z, bsh);
     }
 }
 
@@ -367,9 +367,6 @@ int launch_batch_gather(ppm_batch* b, const GatherArgs& a, const BatchArgs& bt)
     const int m = b->prm.mapping;
     if (m == 1) k_batch_gather<NCH, NTC, NORMALS, VCM, 1><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
     else if (m == 2) k_batch_gather<NCH, NTC, NORMALS, VCM, 2><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
-    else if (m == 5) k_batch_gather<NCH, NTC, NORMALS, VCM, 5><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
-    else if (m == 6) k_batch_gather<NCH, NTC, NORMALS, VCM, 6><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
-    else if (m == 7) k_batch_gather<NCH, NTC, NORMALS, VCM, 7><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
     else if (m == 3 && NTC == 1) k_batch_gather<NCH, 1, NORMALS, VCM, 3><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
     else if (m == 4 && NCH == 1) launch_batch_warp_per_hit<NCH, NTC, NORMALS, VCM>(b, a, bt);
     else k_batch_gather<NCH, NTC, NORMALS, VCM, 0><<<b->gather_grid, kThreads, 0, b->st>>>(a, bt);
@@ -385,9 +382,6 @@ int gather_occupancy(ppm_batch* b)
     cudaError_t e;
     if (m == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gather<NCH, NTC, NORMALS, VCM, 1>, kThreads, 0);
     else if (m == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gather<NCH, NTC, NORMALS, VCM, 2>, kThreads, 0);
-    else if (m == 5) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gather<NCH, NTC, NORMALS, VCM, 5>, kThreads, 0);
-    else if (m == 6) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gather<NCH, NTC, NORMALS, VCM, 6>, kThreads, 0);
-    else if (m == 7) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gather<NCH, NTC, NORMALS, VCM, 7>, kThreads, 0);
     else if (m == 3 && NTC == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gather<NCH, 1, NORMALS, VCM, 3>, kThreads, 0);
     else if (m == 4 && NCH == 1) e = batch_warp_per_hit_occupancy<NCH, NTC, NORMALS, VCM>(&per_sm);
     else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gather<NCH, NTC, NORMALS, VCM, 0>, kThreads, 0);
@@ -566,7 +560,7 @@ int ppm_batch_create(int32_t n_problems, const ppm_hitpoints* hp, const float* r
     if (!(prm.rmin_ratio >= 0.f && prm.rmin_ratio < 1.f)) return PPM_EINVAL;
     if (prm.channels != 1 && prm.channels != 3) return PPM_EINVAL;
     if (prm.rgb_test && prm.channels != 3) return PPM_EINVAL;
-    if (prm.mapping < 0 || prm.mapping > 7 || prm.n_vm < 0.f) return PPM_EINVAL;
+    if (prm.mapping < 0 || prm.mapping > 4 || prm.n_vm < 0.f) return PPM_EINVAL;
     if ((prm.mapping == 3 && prm.rgb_test) || (prm.mapping == 4 && prm.channels == 3)) return PPM_EINVAL;
     if (prm.test != 0) return PPM_EINVAL;   // the count test runs in contexts only
     if (prm.tile < 0 || prm.tile > 1024 || prm.tile % kThreads != 0) return PPM_EINVAL;

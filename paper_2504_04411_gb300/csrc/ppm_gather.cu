@@ -81,13 +81,6 @@ int launch_gather(ppm_ctx* c, const GatherArgs& a, const Prob& pr)
         k_gather_update<NCH, NTC, NORMALS, VCM, 1><<<nb, kThreads, 0, c->stream>>>(a, pr);
     else if (m == 2)
         k_gather_update<NCH, NTC, NORMALS, VCM, 2><<<nb, kThreads, 0, c->stream>>>(a, pr);
-    else if (m == 5)
-        k_gather_update<NCH, NTC, NORMALS, VCM, 5><<<nb, kThreads, 0, c->stream>>>(a, pr);
-    else if (m == 6)
-        k_gather_update<NCH, NTC, NORMALS, VCM, 6><<<nb, kThreads, 0, c->stream>>>(a, pr);
-    else if (m == 7)   // two hit points a thread
-        k_gather_update<NCH, NTC, NORMALS, VCM, 7><<<(unsigned)((c->nh + 2 * kThreads - 1) / (2 * kThreads)),
-                                                     kThreads, 0, c->stream>>>(a, pr);
     else if (m == 3 && NTC == 1)   // traversal 3 tests one channel
         k_gather_update<NCH, 1, NORMALS, VCM, 3><<<nb, kThreads, 0, c->stream>>>(a, pr);
     else if (m == 4 && NCH == 1)   // traversal 4 gathers one flux channel

@@ -19,8 +19,8 @@ constexpr int kWarps = kThreads / 32;
 // cap the resident blocks anyway (and whose sums need the registers)
 template <int MAPPING, int NTC = 1>
 constexpr int kMinBlocks =
-    (MAPPING == 0 || MAPPING == 5 ? 8 : (MAPPING == 1 || MAPPING == 4 || MAPPING == 6 ? 6 : (MAPPING == 2 ? 4 : 5))) *
-    (128 / kThreads) / (NTC == 3 ? 2 : 1);
+    (MAPPING == 0 ? 8 : (MAPPING == 1 || MAPPING == 4 ? 6 : (MAPPING == 2 ? 4 : 5))) * (128 / kThreads) /
+    (NTC == 3 ? 2 : 1);
 constexpr int kNormalDotMin = 8064;   // 127^2 / 2: cosine > ~0.5
 
 // rec1 and aux of an in-disk photon: side by side (aux = rec1 + 1, a stride
@@ -79,36 +79,16 @@ struct Prob {
 // coefficient of variation of the group sums, max_g c_g/C.
 constexpr int kFeatures = 12;
 
-template <int NTC, int SLOTS = kThreads>
+template <int NTC>
 struct Smem {
-    uint32_t c[PPM_NG][SLOTS];
-    float2 SQ[NTC][PPM_NG][SLOTS];      // (sum psi, sum psi^2)
+    uint32_t c[PPM_NG][kThreads];
+    float2 SQ[NTC][PPM_NG][kThreads];   // (sum psi, sum psi^2)
 };
 
 template <int QCAP>
 struct UnionSmem {
     float4 chunk[kWarps][32];
     uint32_t queue[kWarps][QCAP][32];   // per-lane in-disk queues
-};
-
-// traversal 5: per-lane queues of in-disk photons, [slot][lane] so a
-// warp's stores and loads of one slot hit 32 distinct banks
-constexpr int kLockQ = 32;         // queue slots per lane
-constexpr int kLockStep = 4;       // candidates a lane tests between two warp votes
-
-struct LockQueue {
-    uint32_t q[kWarps][kLockQ][32];
-};
-
-// traversal 6: per warp, the current hit point's non-empty runs of photons
-// (rows of its cell box set up by the lanes in parallel) and the in-disk
-// photons found but not yet classified, compacted: (offsets, psi) and index
-constexpr int kMaxRuns = 128;      // 8 x 8 rows of a cell box, two hash-block runs each
-struct WarpHitSmem {
-    uint32_t run_s[kMaxRuns];
-    uint32_t run_n[kMaxRuns];
-    float4 pd[64];                 // (dx, dy, dz, psi) of a queued pair
-    uint32_t pp[64];               // its photon index
 };
 
 // this thread's hit point
@@ -359,115 +339,6 @@ __device__ void gather_own(const GatherArgs& a, const Hit& H, const GridGeom& G,
     }
 }
 
-// traversal 5, drain: every lane classifies its queued in-disk photons in
-// queue order (its walk order), the warp in lockstep up to the longest
-// queue; the next entry's record is loaded before the current one is used
-template <int NCH, int NTC, bool NORMALS, bool VCM, bool BATCH>
-__device__ __forceinline__ void drain_lockstep(const GatherArgs& a, const Hit& H, Smem<NTC>& sm,
-                                               LockQueue& lq, int w, int lane, int tid,
-                                               Acc<NCH>& acc, int qlen)
-{
-    const int qmax = __reduce_max_sync(0xffffffffu, qlen);
-    uint32_t pn = 0u;
-    float4 Xn = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (qlen > 0) { pn = lq.q[w][0][lane]; Xn = __ldg(a.rec0 + pn); }
-    for (int k = 0; k < qmax; ++k) {
-        const uint32_t p = pn;
-        const float4 X = Xn;
-        if (k + 1 < qlen) { pn = lq.q[w][k + 1][lane]; Xn = __ldg(a.rec0 + pn); }
-        if (k < qlen) {
-            float dx, dy, dz;
-            in_disk(H, X, dx, dy, dz);
-            gather_pair<NCH, NTC, NORMALS, VCM, BATCH>(a, H, sm, tid, acc, p, X, dx, dy, dz);
-        }
-    }
-    flush_run<NCH, NTC>(acc);
-    __syncwarp();
-}
-
-// Traversal 5: the warp walks the rows of its lanes' cell boxes in step
-// (row (dz, dy) of every lane's own box at once), each lane its own trimmed
-// runs, kLockStep candidates at a time between warp votes; in-disk photons
-// go to the lane's queue and are classified in lockstep whenever a queue
-// could overflow and at the end.  A lane's photons are classified in the
-// order traversal 0 visits them, so its sums are bit-identical to it.
-template <int NCH, int NTC, bool NORMALS, bool VCM, bool BATCH>
-__device__ void gather_lockstep(const GatherArgs& a, const Hit& H, const GridGeom& G, CellBox b, bool live,
-                                Smem<NTC>& sm, LockQueue& lq, int tid, int lane, int w, Acc<NCH>& acc)
-{
-    const unsigned full = 0xffffffffu;
-    const int B = 1 << G.lb;
-    if (live && (b.ix1 - b.ix0 >= B || b.iy1 - b.iy0 >= B || b.iz1 - b.iz0 >= B)) {
-        atomicOr(a.err, 1);
-        b.ix1 = min(b.ix1, b.ix0 + B - 1); b.iy1 = min(b.iy1, b.iy0 + B - 1); b.iz1 = min(b.iz1, b.iz0 + B - 1);
-    }
-    const RowCull rcu = row_cull(H, G, b);
-    const int nz = live ? b.iz1 - b.iz0 + 1 : 0;
-    const int ny = live ? b.iy1 - b.iy0 + 1 : 0;
-    const int NZ = __reduce_max_sync(full, nz);
-    const int NY = __reduce_max_sync(full, ny);
-    int qlen = 0;
-    for (int dz = 0; dz < NZ; ++dz) {
-        const int iz = b.iz0 + dz;
-        float rz2 = -1.f;
-        if (dz < nz) {
-            const float gz = slab_gap(H.P.z, iz, G, rcu.eps);
-            rz2 = rcu.rc2 - gz * gz;
-        }
-        for (int dy = 0; dy < NY; ++dy) {
-            const int iy = b.iy0 + dy;
-            // this lane's photons of row (iy, iz): at most two hash-block runs
-            uint32_t s0 = 0u, n0 = 0u, s1 = 0u, n = 0u;
-            if (dy < ny && rz2 + rcu.slack >= 0.f) {
-                const float gy = slab_gap(H.P.y, iy, G, rcu.eps);
-                const float ryz2 = rz2 - gy * gy;
-                if (ryz2 + rcu.slack >= 0.f) {
-                    const float half = sqrtf(fmaxf(ryz2, 0.f) + rcu.slack) + rcu.eps;
-                    const int xa = max(b.ix0, ppm_cell_coord(__fsub_rn(H.P.x, half), G.inv_h));
-                    const int xb = min(b.ix1, ppm_cell_coord(__fadd_rn(H.P.x, half), G.inv_h));
-                    if (xa <= xb) {
-                        const int ixe = min(xb, xa | (B - 1));
-                        const uint32_t b0 = ppm_bucket(xa, iy, iz, G);
-                        s0 = __ldg(a.cell_start + b0);
-                        n0 = __ldg(a.cell_start + b0 + (uint32_t)(ixe - xa) + 1u) - s0;
-                        n = n0;
-                        if (ixe < xb) {
-                            const uint32_t b1 = ppm_bucket(ixe + 1, iy, iz, G);
-                            s1 = __ldg(a.cell_start + b1);
-                            n += __ldg(a.cell_start + b1 + (uint32_t)(xb - ixe - 1) + 1u) - s1;
-                        }
-                    }
-                }
-            }
-            acc.cand += n;
-            const uint32_t N = __reduce_max_sync(full, n);
-            for (uint32_t k0 = 0; k0 < N; k0 += kLockStep) {
-                float4 X[kLockStep];
-                uint32_t pk[kLockStep];
-#pragma unroll
-                for (int j = 0; j < kLockStep; ++j) {
-                    const uint32_t k = k0 + (uint32_t)j;
-                    pk[j] = k < n0 ? s0 + k : s1 + (k - n0);
-                    X[j] = k < n ? __ldg(a.rec0 + pk[j]) : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-#pragma unroll
-                for (int j = 0; j < kLockStep; ++j) {
-                    float dx, dy2, dz2;
-                    if (k0 + (uint32_t)j < n && in_disk(H, X[j], dx, dy2, dz2)) {
-                        lq.q[w][qlen][lane] = pk[j];
-                        ++qlen;
-                    }
-                }
-                if (__any_sync(full, qlen > kLockQ - kLockStep)) {
-                    drain_lockstep<NCH, NTC, NORMALS, VCM, BATCH>(a, H, sm, lq, w, lane, tid, acc, qlen);
-                    qlen = 0;
-                }
-            }
-        }
-    }
-    drain_lockstep<NCH, NTC, NORMALS, VCM, BATCH>(a, H, sm, lq, w, lane, tid, acc, qlen);
-}
-
 // traversal 1, drain: each lane processes its queued in-disk photons in
 // queue (= traversal) order; the warp loops to the longest queue
 template <int NCH, int NTC, bool NORMALS, bool VCM, bool BATCH, typename US>
@@ -519,14 +390,11 @@ struct FixSmem {
 
 template <int NCH, int NTC, int MAPPING>
 struct BlockShared {
-    typename std::conditional<MAPPING == 3, Empty,
-                              typename std::conditional<MAPPING == 7, Smem<NTC, 2 * kThreads>, Smem<NTC>>::type>::type sm;
-    typename std::conditional<MAPPING == 5, LockQueue, Empty>::type lq;
+    typename std::conditional<MAPPING == 3, Empty, Smem<NTC>>::type sm;
     typename std::conditional<MAPPING == 1 || MAPPING == 2, UnionSmem<MAPPING == 2 ? 64 : 32>, Empty>::type us;
     typename std::conditional<MAPPING == 3, PairSmem, Empty>::type ps;
     typename std::conditional<MAPPING == 3, FixSmem<NCH>, Empty>::type fx;
-    typename std::conditional<MAPPING == 4 || MAPPING == 6, Smem<NTC>, Empty>::type lp;   // lanes' partial sums
-    typename std::conditional<MAPPING == 6, WarpHitSmem[kWarps], Empty>::type wh;
+    typename std::conditional<MAPPING == 4, Smem<NTC>, Empty>::type lp;   // lanes' partial sums
 };
 
 // this iteration's sums of one hit point, read where they are kept
@@ -887,147 +755,6 @@ __device__ __forceinline__ void gather_warp_hit(const GatherArgs& a, const Hit& 
     if ((lane & 1) == 0 && (lane >> 1) < PPM_NG) sm.c[lane >> 1][owner] = ct;
 }
 
-// Traversal 6: hit point Hj (lane j's, owner thread `owner`) by the whole
-// warp.  The lanes set up the rows of its cell box in parallel (one row a
-// lane) and list the non-empty runs in row order; the warp then tests 32
-// consecutive candidates a step and compacts the in-disk ones into a queue,
-// and whenever 32 are queued every lane classifies one of them into its own
-// column of lp (so the classification runs with all lanes busy).  At the end
-// the columns are reduced over the warp into the owner's slots of sm; the
-// RGB flux sums of a luminance test go to the owner's acc.
-template <int NCH, int NTC, bool NORMALS, bool VCM, bool BATCH>
-__device__ __forceinline__ void gather_warp_hit_compact(const GatherArgs& a, const Hit& Hj, const GridGeom& G,
-                                                        CellBox b, Smem<NTC>& lp, Smem<NTC>& sm,
-                                                        WarpHitSmem& wh, int tid, int lane, int owner,
-                                                        Acc<NCH>& acc)
-{
-    const unsigned full = 0xffffffffu;
-    const unsigned lt = (1u << lane) - 1u;
-    const int B = 1 << G.lb;
-    if (b.ix1 - b.ix0 >= B || b.iy1 - b.iy0 >= B || b.iz1 - b.iz0 >= B) {
-        if (lane == 0) atomicOr(a.err, 1);
-        b.ix1 = min(b.ix1, b.ix0 + B - 1); b.iy1 = min(b.iy1, b.iy0 + B - 1); b.iz1 = min(b.iz1, b.iz0 + B - 1);
-    }
-    const RowCull rcu = row_cull(Hj, G, b);
-    const int ny = b.iy1 - b.iy0 + 1;
-    const int nrows = ny * (b.iz1 - b.iz0 + 1);
-    // runs of the rows, (iz, iy) in the order traversal 0 visits them
-    int nruns = 0;
-    for (int r0 = 0; r0 < nrows; r0 += 32) {
-        const int r = r0 + lane;
-        uint32_t s0 = 0u, n0 = 0u, s1 = 0u, n1 = 0u;
-        if (r < nrows) {
-            const int iz = b.iz0 + r / ny, iy = b.iy0 + r % ny;
-            int xa, xb;
-            row_xrange(Hj, G, b, rcu, true, iy, iz, xa, xb);
-            if (xa <= xb) {
-                const int ixe = min(xb, xa | (B - 1));
-                const uint32_t b0 = ppm_bucket(xa, iy, iz, G);
-                s0 = __ldg(a.cell_start + b0);
-                n0 = __ldg(a.cell_start + b0 + (uint32_t)(ixe - xa) + 1u) - s0;
-                if (ixe < xb) {
-                    const uint32_t b1 = ppm_bucket(ixe + 1, iy, iz, G);
-                    s1 = __ldg(a.cell_start + b1);
-                    n1 = __ldg(a.cell_start + b1 + (uint32_t)(xb - ixe - 1) + 1u) - s1;
-                }
-            }
-        }
-        const int k = (n0 > 0u ? 1 : 0) + (n1 > 0u ? 1 : 0);
-        int inc = k;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(full, inc, o);
-            if (lane >= o) inc += y;
-        }
-        int at = nruns + inc - k;
-        if (n0 > 0u) { wh.run_s[at] = s0; wh.run_n[at] = n0; ++at; }
-        if (n1 > 0u) { wh.run_s[at] = s1; wh.run_n[at] = n1; }
-        nruns += __shfl_sync(full, inc, 31);
-    }
-    __syncwarp();
-    Acc<NCH> la;                       // this lane's RGB flux sums of Hj
-#pragma unroll
-    for (int c = 0; c < NCH; ++c) { la.phi[c] = 0.f; la.comp[c] = 0.f; la.part[c] = 0.f; }
-    int qn = 0;                        // queued pairs (warp-uniform)
-    for (int ri = 0; ri < nruns; ++ri) {
-        const uint32_t s = wh.run_s[ri], n = wh.run_n[ri];
-        if (lane == 0) acc.cand += n;
-        for (uint32_t k0 = 0; k0 < n; k0 += 32u) {
-            const uint32_t k = k0 + (uint32_t)lane;
-            float dx = 0.f, dy = 0.f, dz = 0.f;
-            float4 X = make_float4(0.f, 0.f, 0.f, 0.f);
-            bool in = false;
-            if (k < n) {
-                X = __ldg(a.rec0 + s + k);
-                in = in_disk(Hj, X, dx, dy, dz);
-            }
-            const unsigned bal = __ballot_sync(full, in);
-            if (in) {
-                const int at = qn + __popc(bal & lt);
-                wh.pd[at] = make_float4(dx, dy, dz, X.w);
-                wh.pp[at] = s + k;
-            }
-            qn += __popc(bal);
-            if (qn >= 32) {
-                __syncwarp();
-                const float4 D = wh.pd[lane];
-                const uint32_t p = wh.pp[lane];
-                float4 Dn = make_float4(0.f, 0.f, 0.f, 0.f);
-                uint32_t pn = 0u;
-                if (lane < qn - 32) { Dn = wh.pd[32 + lane]; pn = wh.pp[32 + lane]; }
-                __syncwarp();
-                if (lane < qn - 32) { wh.pd[lane] = Dn; wh.pp[lane] = pn; }
-                qn -= 32;
-                gather_pair<NCH, NTC, NORMALS, VCM, BATCH>(a, Hj, lp, tid, la, p, D, D.x, D.y, D.z);
-                flush_run<NCH, NTC>(la);
-                __syncwarp();
-            }
-        }
-    }
-    __syncwarp();
-    if (lane < qn) {
-        const float4 D = wh.pd[lane];
-        gather_pair<NCH, NTC, NORMALS, VCM, BATCH>(a, Hj, lp, tid, la, wh.pp[lane], D, D.x, D.y, D.z);
-    }
-    flush_run<NCH, NTC>(la);
-    __syncwarp();
-    // the lanes' columns -> the owner's slots (and cleared for the next hit point)
-#pragma unroll
-    for (int c = 0; c < NTC; ++c) {
-        float v[32];
-#pragma unroll
-        for (int g = 0; g < PPM_NG; ++g) {
-            const float2 q = lp.SQ[c][g][tid];
-            v[g] = q.x;
-            v[PPM_NG + g] = q.y;
-            lp.SQ[c][g][tid] = make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int i = 2 * PPM_NG; i < 32; ++i) v[i] = 0.f;
-        const float t = warp_reduce_scatter<32>(v, lane);        // lane l: value l
-        if (lane < PPM_NG) sm.SQ[c][lane][owner].x = t;
-        else if (lane < 2 * PPM_NG) sm.SQ[c][lane - PPM_NG][owner].y = t;
-    }
-    uint32_t cc[16];
-#pragma unroll
-    for (int g = 0; g < PPM_NG; ++g) { cc[g] = lp.c[g][tid]; lp.c[g][tid] = 0u; }
-#pragma unroll
-    for (int i = PPM_NG; i < 16; ++i) cc[i] = 0u;
-    const uint32_t ct = warp_reduce_scatter<16>(cc, lane);    // lane l: count l / 2
-    if ((lane & 1) == 0 && (lane >> 1) < PPM_NG) sm.c[lane >> 1][owner] = ct;
-    if constexpr (NCH == 3 && NTC == 1) {
-        // the lanes' compensated RGB sums, added over the warp
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            float f = la.phi[c] - la.comp[c];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(full, f, o);
-            if (lane == (owner & 31)) { acc.phi[c] = f; acc.comp[c] = 0.f; }
-        }
-    }
-    __syncwarp();
-}
-
 // The hit points [h0, h_end) (at most one block's worth, h0 + tid for this
 // thread) of problem pr: gather, test, update; block-wide reductions into
 // pr's counters.  Ends with a block barrier, so it can be called in a loop.
@@ -1054,7 +781,7 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
 #pragma unroll
             for (int c = 0; c < NTC; ++c) sm.SQ[c][g][tid] = make_float2(0.f, 0.f);
         }
-        if constexpr (MAPPING == 4 || MAPPING == 6) {
+        if constexpr (MAPPING == 4) {
 #pragma unroll
             for (int g = 0; g < PPM_NG; ++g) {
                 bsh.lp.c[g][tid] = 0u;
@@ -1105,32 +832,6 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
     const FixScale fs = fix_scale(MAPPING == 3 ? G.psimax : 1.f);
     if constexpr (MAPPING == 0) {
         if (live) gather_own<NCH, NTC, NORMALS, VCM, BATCH>(a, H, G, b, sm, tid, acc);
-    } else if constexpr (MAPPING == 5) {
-        __syncwarp();
-        if (__any_sync(0xffffffffu, live))
-            gather_lockstep<NCH, NTC, NORMALS, VCM, BATCH>(a, H, G, b, live, sm, bsh.lq, tid, lane, w, acc);
-    } else if constexpr (MAPPING == 6) {
-        __syncwarp();
-        for (int j = 0; j < 32; ++j) {
-            if (!__shfl_sync(0xffffffffu, (int)live, j)) continue;   // warp-uniform
-            Hit Hj;
-            Hj.P = shfl_f4(H.P, j);
-            Hj.U = shfl_f4(H.U, j);
-            Hj.V = shfl_f4(H.V, j);
-            Hj.r = __shfl_sync(0xffffffffu, H.r, j);
-            Hj.r2 = __shfl_sync(0xffffffffu, H.r2, j);
-            Hj.inv_eta = __shfl_sync(0xffffffffu, H.inv_eta, j);
-            Hj.nqh = __shfl_sync(0xffffffffu, H.nqh, j);
-            Hj.pid = H.pid;
-            CellBox bj;
-            bj.ix0 = __shfl_sync(0xffffffffu, b.ix0, j); bj.ix1 = __shfl_sync(0xffffffffu, b.ix1, j);
-            bj.iy0 = __shfl_sync(0xffffffffu, b.iy0, j); bj.iy1 = __shfl_sync(0xffffffffu, b.iy1, j);
-            bj.iz0 = __shfl_sync(0xffffffffu, b.iz0, j); bj.iz1 = __shfl_sync(0xffffffffu, b.iz1, j);
-            bj.rc = __shfl_sync(0xffffffffu, b.rc, j);
-            gather_warp_hit_compact<NCH, NTC, NORMALS, VCM, BATCH>(a, Hj, G, bj, bsh.lp, sm, bsh.wh[w], tid,
-                                                                   lane, w * 32 + j, acc);
-        }
-        __syncwarp();
     } else if constexpr (MAPPING == 4) {
         __syncwarp();
         for (int j = 0; j < 32; ++j) {
@@ -1350,190 +1051,6 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
     __syncthreads();
 }
 
-// this iteration's sums of slot `slot` of a block's slots (traversal 7)
-template <int NTC, int SLOTS>
-struct SlotSums {
-    const Smem<NTC, SLOTS>& sm;
-    int slot;
-    __device__ __forceinline__ float S(int c, int g) const { return sm.SQ[c][g][slot].x; }
-    __device__ __forceinline__ float Q(int c, int g) const { return sm.SQ[c][g][slot].y; }
-    __device__ __forceinline__ uint32_t C(int g) const { return sm.c[g][slot]; }
-};
-
-// one hit point of traversal 7: loaded, its cull box, or a dead slot
-__device__ __forceinline__ void load_hit(const GatherArgs& a, const Prob& pr, const GridGeom& G, int64_t h,
-                                         bool live, uint32_t pid, Hit& H, CellBox& b)
-{
-    H.pid = pid;
-    H.inv_eta = 0.f;
-    if (live) {
-        H.P = a.hp_pos[h];
-        H.U = a.hp_u[h];
-        H.V = a.hp_v[h];
-        H.r = a.r[h];
-        H.r2 = __fmul_rn(H.r, H.r);
-        H.nqh = __float_as_uint(H.P.w);
-        b = cell_box(H, G);
-    } else {
-        H.P = make_float4(0.f, 0.f, 0.f, 0.f);
-        H.U = H.V = H.P;
-        H.nqh = 0u;
-        H.r = 0.f;
-        H.r2 = -1.f;                      // no photon passes d2 <= -1
-        b = CellBox{INT_MAX, INT_MIN, INT_MAX, INT_MIN, INT_MAX, INT_MIN, 0.f};
-    }
-}
-
-// Traversal 7: two neighbouring hit points a thread (slots 2 tid and
-// 2 tid + 1 of the block's 2 kThreads; consecutive along the Hilbert curve,
-// so their disks overlap almost entirely).  The thread walks the cells of
-// both boxes once -- rows trimmed to a sphere that holds both cull spheres
-// -- and tests every photon it loads against both disks, so a record load
-// and the loop around it serve two tests.  Each hit point's in-disk photons
-// are classified in the order of traversal 0's walk (the walk covers its
-// own trimmed rows in the same order), so the group sums are bit-identical
-// to traversal 0's (the RGB flux sums of a luminance test split into runs
-// differently).  A pair whose joint box spans more than a hash block walks
-// each hit point on its own.
-template <int NCH, int NTC, bool NORMALS, bool VCM, bool BATCH>
-__device__ __forceinline__ void gather_block_pair(const GatherArgs& a, const Prob& pr, int64_t h0, int64_t h_end,
-                                                  BlockShared<NCH, NTC, 7>& bsh)
-{
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    auto& sm = bsh.sm;
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int slot = 2 * tid + k;
-#pragma unroll
-        for (int g = 0; g < PPM_NG; ++g) {
-            sm.c[g][slot] = 0u;
-#pragma unroll
-            for (int c = 0; c < NTC; ++c) sm.SQ[c][g][slot] = make_float2(0.f, 0.f);
-        }
-    }
-    GridGeom G = *pr.geom;
-    if constexpr (!BATCH) G.pid = 0u;
-    const uint32_t pid = BATCH ? pr.pid : 0u;
-    const int64_t ha = h0 + 2 * tid, hb = ha + 1;
-    const bool la = ha < h_end, lb = hb < h_end;
-    Hit A, Bh;
-    CellBox ba, bb;
-    load_hit(a, pr, G, ha, la, pid, A, ba);
-    load_hit(a, pr, G, hb, lb, pid, Bh, bb);
-    if constexpr (VCM) {
-        if (la) A.inv_eta = __frcp_rn(__fmul_rn(__fmul_rn(pr.n_vm, 3.14159265358979f), A.r2));
-        if (lb) Bh.inv_eta = __frcp_rn(__fmul_rn(__fmul_rn(pr.n_vm, 3.14159265358979f), Bh.r2));
-    }
-    Acc<NCH> acc_a, acc_b;
-#pragma unroll
-    for (int c = 0; c < NCH; ++c) {
-        acc_a.phi[c] = acc_a.comp[c] = acc_a.part[c] = 0.f;
-        acc_b.phi[c] = acc_b.comp[c] = acc_b.part[c] = 0.f;
-    }
-    const int Bk = 1 << G.lb;
-    const int sa = 2 * tid, sb = 2 * tid + 1;
-    // the joint box, or each hit point on its own
-    CellBox bj{min(ba.ix0, bb.ix0), max(ba.ix1, bb.ix1), min(ba.iy0, bb.iy0), max(ba.iy1, bb.iy1),
-               min(ba.iz0, bb.iz0), max(ba.iz1, bb.iz1), 0.f};
-    const bool joint = la && lb && bj.ix1 - bj.ix0 < Bk && bj.iy1 - bj.iy0 < Bk && bj.iz1 - bj.iz0 < Bk;
-    if (!joint) {
-        if (la) gather_own<NCH, NTC, NORMALS, VCM, BATCH>(a, A, G, ba, sm, sa, acc_a);
-        if (lb) gather_own<NCH, NTC, NORMALS, VCM, BATCH>(a, Bh, G, bb, sm, sb, acc_b);
-    } else {
-        // a sphere holding both cull spheres: centre at the midpoint, radius
-        // the larger cull radius plus half the distance (rounded up)
-        Hit M = A;
-        M.P.x = 0.5f * (A.P.x + Bh.P.x);
-        M.P.y = 0.5f * (A.P.y + Bh.P.y);
-        M.P.z = 0.5f * (A.P.z + Bh.P.z);
-        const float ddx = A.P.x - Bh.P.x, ddy = A.P.y - Bh.P.y, ddz = A.P.z - Bh.P.z;
-        const float half = 0.5f * sqrtf(fmaf(ddz, ddz, fmaf(ddy, ddy, ddx * ddx)));
-        bj.rc = fmaxf(ba.rc, bb.rc) + half * 1.0009765625f + (fabsf(M.P.x) + fabsf(M.P.y) + fabsf(M.P.z)) * 1.0e-6f;
-        const RowCull rcu = row_cull(M, G, bj);
-        for (int iz = bj.iz0; iz <= bj.iz1; ++iz) {
-            const float gz = slab_gap(M.P.z, iz, G, rcu.eps);
-            const float rz2 = rcu.rc2 - gz * gz;
-            if (rz2 + rcu.slack < 0.f) continue;
-            for (int iy = bj.iy0; iy <= bj.iy1; ++iy) {
-                const float gy = slab_gap(M.P.y, iy, G, rcu.eps);
-                const float ryz2 = rz2 - gy * gy;
-                if (ryz2 + rcu.slack < 0.f) continue;
-                const float hw = sqrtf(fmaxf(ryz2, 0.f) + rcu.slack) + rcu.eps;
-                const int xa = max(bj.ix0, ppm_cell_coord(__fsub_rn(M.P.x, hw), G.inv_h));
-                const int xb = min(bj.ix1, ppm_cell_coord(__fadd_rn(M.P.x, hw), G.inv_h));
-                int ix = xa;
-                while (ix <= xb) {
-                    const int ixe = min(xb, ix | (Bk - 1));
-                    const uint32_t b0 = ppm_bucket(ix, iy, iz, G);
-                    const uint32_t s = __ldg(a.cell_start + b0);
-                    const uint32_t e = __ldg(a.cell_start + b0 + (uint32_t)(ixe - ix) + 1u);
-                    acc_a.cand += e - s;
-                    float4 Xn = s < e ? __ldg(a.rec0 + s) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    for (uint32_t p = s; p < e; ++p) {
-                        const float4 X = Xn;
-                        if (p + 1u < e) Xn = __ldg(a.rec0 + p + 1u);
-                        float dx, dy, dz;
-                        if (in_disk(A, X, dx, dy, dz))
-                            gather_pair<NCH, NTC, NORMALS, VCM, BATCH>(a, A, sm, sa, acc_a, p, X, dx, dy, dz);
-                        if (in_disk(Bh, X, dx, dy, dz))
-                            gather_pair<NCH, NTC, NORMALS, VCM, BATCH>(a, Bh, sm, sb, acc_b, p, X, dx, dy, dz);
-                    }
-                    if (e > s) { flush_run<NCH, NTC>(acc_a); flush_run<NCH, NTC>(acc_b); }
-                    ix = ixe + 1;
-                }
-            }
-        }
-    }
-    flush_run<NCH, NTC>(acc_a);
-    flush_run<NCH, NTC>(acc_b);
-
-    float r_new = 0.f, r_nb = 0.f;
-    unsigned long long rej = 0, pairs = 0;
-    if (la) update_hit<NCH, NTC, false, false>(a, pr, SlotSums<NTC, 2 * kThreads>{sm, sa}, ha, A.r, acc_a, r_new,
-                                               rej, pairs);
-    if (lb) update_hit<NCH, NTC, false, false>(a, pr, SlotSums<NTC, 2 * kThreads>{sm, sb}, hb, Bh.r, acc_b, r_nb,
-                                               rej, pairs);
-    r_new = fmaxf(r_new, r_nb);
-
-    __shared__ float s_rmax[kWarps];
-    __shared__ unsigned long long s_cnt3[3][kWarps];
-    const float wm = warp_max(r_new);
-    const unsigned long long wp = warp_sum_u64(pairs), wc = warp_sum_u64(acc_a.cand + acc_b.cand),
-                             wr = warp_sum_u64(rej);
-    if (lane == 0) {
-        s_rmax[w] = wm;
-        s_cnt3[0][w] = wp; s_cnt3[1][w] = wc; s_cnt3[2][w] = wr;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        float m = 0.f;
-        unsigned long long pp = 0, c = 0, j = 0;
-#pragma unroll
-        for (int ww = 0; ww < kWarps; ++ww) {
-            m = fmaxf(m, s_rmax[ww]); pp += s_cnt3[0][ww]; c += s_cnt3[1][ww]; j += s_cnt3[2][ww];
-        }
-        atomicMax((int*)pr.rmax_next, __float_as_int(m));
-        atomicAdd(pr.counters + 0, pp);
-        atomicAdd(pr.counters + 1, c);
-        atomicAdd(pr.counters + 2, j);
-        atomicAdd(pr.counters + 3, pp);
-    }
-    __syncthreads();
-}
-
-// hit points [h0, h_end) of a block with the traversal's hit points per block
-template <int NCH, int NTC, bool NORMALS, bool VCM, int MAPPING, bool BATCH, bool FEAT = false, bool CHI2 = false>
-__device__ __forceinline__ void gather_any_block(const GatherArgs& a, const Prob& pr, int64_t h0, int64_t h_end,
-                                                 BlockShared<NCH, NTC, MAPPING>& bsh)
-{
-    if constexpr (MAPPING == 7) gather_block_pair<NCH, NTC, NORMALS, VCM, BATCH>(a, pr, h0, h_end, bsh);
-    else gather_block<NCH, NTC, NORMALS, VCM, MAPPING, BATCH, FEAT, CHI2>(a, pr, h0, h_end, bsh);
-}
-
-// hit points a block handles
-template <int MAPPING>
-constexpr int kHitsPerBlock = MAPPING == 7 ? 2 * kThreads : kThreads;
-
 // one context: one block per kThreads hit points
 template <int NCH, int NTC, bool NORMALS, bool VCM, int MAPPING, bool FEAT = false, bool CHI2 = false>
 __global__ void __launch_bounds__(kThreads, kMinBlocks<MAPPING, NTC>)
@@ -1541,8 +1058,8 @@ k_gather_update(GatherArgs a, Prob pr)
 {
     __shared__ BlockShared<NCH, NTC, MAPPING> bsh;
     if (*a.err & 4) return;          // the grid's sort gave up: no usable grid
-    const int64_t h0 = (int64_t)blockIdx.x * kHitsPerBlock<MAPPING>;
-    gather_any_block<NCH, NTC, NORMALS, VCM, MAPPING, false, FEAT, CHI2>(a, pr, h0, a.nh, bsh);
+    const int64_t h0 = (int64_t)blockIdx.x * kThreads;
+    gather_block<NCH, NTC, NORMALS, VCM, MAPPING, false, FEAT, CHI2>(a, pr, h0, a.nh, bsh);
 }
 
 }  // namespace

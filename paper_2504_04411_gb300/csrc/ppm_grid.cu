@@ -216,8 +216,7 @@ int ppm_grid_build(ppm_ctx* c, const ppm_photons* ph)
     if (rc) return rc;
     // hash blocks of 4^3 cells suffice for one sphere (<= 4 cells per axis at
     // cell_factor >= 1); the warp-union traversal and cell_factor < 1 need 8^3
-    const int m = c->prm.mapping;
-    const int lb = (c->prm.cell_factor >= 1.0f && (m == 0 || m == 5 || m == 6)) ? 2 : 3;   // joint / union walks: 8^3
+    const int lb = (c->prm.cell_factor >= 1.0f && c->prm.mapping == 0) ? 2 : 3;   // union traversals: 8^3
     c->tbits = ppm_table_bits(n, lb);
     const uint32_t T = 1u << c->tbits;
     if ((int64_t)T + 1 > c->cs_cap) {

@@ -51,7 +51,7 @@ def _run_batch(scenes, iters, params, cfs=None):
     return hps, phs, states, stats, L, graph
 
 
-@pytest.mark.parametrize("mapping", [0, 1, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("mapping", [0, 1, 3, 4])
 def test_batch_matches_oracle_per_problem(mapping):
     scenes = _problems()
     iters = 4
@@ -65,14 +65,14 @@ def test_batch_matches_oracle_per_problem(mapping):
         assert rep.diverged <= 2
 
 
-@pytest.mark.parametrize("mapping", [0, 1, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("mapping", [0, 1, 3, 4])
 def test_batch_bit_identical_to_single_contexts(mapping):
-    """Traversals 0-3 and 5 visit a hit point's photons in the same order in
-    a batch as in a context, so the state is bit-identical.  Traversals 4 and
-    6 split a hit point's photons over the lanes by position, and a batch's
-    cells can also hold other problems' photons (skipped): the lanes' partial
-    sums, and so the rounding of the window sums, can differ.  Counts,
-    windows, radii and decisions stay identical."""
+    """Traversals 0-3 visit a hit point's photons in the same order in a
+    batch as in a context, so the state is bit-identical.  Traversal 4 splits
+    a cell's photons over the lanes by position, and a batch's cells can
+    also hold other problems' photons (skipped): the lanes' partial sums, and
+    so the rounding of the window sums, can differ.  Counts, windows, radii
+    and decisions stay identical."""
     from paper_2504_04411_gb300 import ppm
     scenes = _problems()
     iters = 4
@@ -85,14 +85,14 @@ def test_batch_bit_identical_to_single_contexts(mapping):
             est.step(phs[i][p])
             one = {k: v.cpu().numpy() for k, v in est.state().items()}
             for k in one:
-                if mapping not in (4, 6) or k in exact:
+                if mapping != 4 or k in exact:
                     assert np.array_equal(one[k], states[i][p][k]), (p, i, k)
                 else:
                     assert np.allclose(one[k], states[i][p][k], rtol=1e-5, atol=1e-6 * np.abs(one[k]).max()), \
                         (p, i, k)
             assert est.stats().pairs == stats[i][p].pairs
         Lc = est.radiance().cpu().numpy()
-        if mapping not in (4, 6):
+        if mapping != 4:
             assert np.array_equal(Lc, L[p])
         else:
             assert np.allclose(Lc, L[p], rtol=1e-5, atol=1e-6 * np.abs(Lc).max())
@@ -179,7 +179,7 @@ def test_batch_windows_beyond_the_initial_critical_value_table():
 
 
 @pytest.mark.parametrize("mode", ["rgb", "rgb_test", "vcm_rgb", "vcm"])
-@pytest.mark.parametrize("mapping", [0, 1, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("mapping", [0, 1, 3, 4])
 def test_batch_rgb_and_vcm_problems_match_oracle(mode, mapping):
     """Batches of RGB problems (luminance test or one test per channel) and
     VCM+ problems (merge weights; RGB or one channel): every problem against

@@ -138,7 +138,7 @@ def test_cppm_argument_checks():
 
 
 # ------------------------------------------ hit points traced anew ------
-@pytest.mark.parametrize("mapping", [0, 1, 4, 5, 6, 7])
+@pytest.mark.parametrize("mapping", [0, 1, 4])
 def test_retraced_hit_points_full_trajectory(mapping):
     """SPPM-style pixels: each iteration's hit points land at a new random
     point of their pixel (ppm_set_hitpoints), statistics carried per pixel;
@@ -185,7 +185,7 @@ def test_set_hitpoints_argument_checks():
 
 
 # --------------------------------------------------------- plane scenes ----
-MAPPINGS = [0, 1, 2, 3, 4, 5, 6, 7]
+MAPPINGS = [0, 1, 2, 3, 4]
 
 
 @pytest.mark.parametrize("mapping", MAPPINGS)
@@ -257,7 +257,7 @@ def test_box_scene_rgb_luminance_test():
     compare(states, stats, L, ref, iters)
 
 
-@pytest.mark.parametrize("mapping", [0, 1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("mapping", [0, 1, 2, 3, 4])
 def test_box_scene_rgb_per_channel_test(mapping):
     """One F-test per RGB channel, reject if any rejects: every channel's
     window sums against the oracle.  Traversal 3 tests one channel and
@@ -553,43 +553,4 @@ def test_vcm_merge_scale_full_size_sampled():
     rep = compare(sub_states, [{"pairs": 0, "flags": 0}] * iters, L[idx], ref, iters, check_pairs=False)
     assert rep.diverged <= 3
     assert ref.pairs.sum() > 50_000
-    torch.cuda.synchronize()
-
-
-@pytest.mark.parametrize("other", [5, 7])
-@pytest.mark.parametrize("rgb,vcm,rgb_test", [(False, False, 0), (True, True, 0), (True, False, 1)])
-def test_traversals_classifying_in_walk_order_are_bit_identical(rgb, vcm, rgb_test, other):
-    """Traversal 5 (rows walked in lockstep, in-disk photons queued and
-    classified in lockstep) and traversal 7 (two hit points a thread, one
-    walk over both boxes) classify each hit point's photons in the order
-    traversal 0 visits them: every state array is bit for bit the same --
-    except, with the luminance test of RGB flux, the estimate tau, whose
-    flux sums each traversal splits into runs at other places (equal to FP32
-    rounding)."""
-    import torch
-    sc = _box(rgb=rgb, vcm=vcm, seed=4)
-    iters = 5
-    hp = sc.hitpoints("cuda")
-    batches = [sc.photons(i, "cuda") for i in range(1, iters + 1)]
-    out = []
-    for mapping in (0, other):
-        p = _params(channels=3 if rgb else 1, vcm=int(vcm), rgb_test=rgb_test, k=0.9 if vcm else 0.7,
-                    mapping=mapping)
-        states, stats, L = run_gpu(hp, batches, sc.r0, params=p)
-        out.append((states, stats, L))
-    (s0, t0, L0), (s5, t5, L5) = out
-    split = rgb and not rgb_test
-    for it in range(iters):
-        for k in s0[it]:
-            if split and k == "tau":
-                assert np.allclose(s0[it][k], s5[it][k], rtol=1e-6, atol=0), (it, k)
-            else:
-                assert np.array_equal(s0[it][k], s5[it][k]), (it, k)
-        assert t0[it]["pairs"] == t5[it]["pairs"]
-        if other == 5:
-            assert t0[it]["candidates"] == t5[it]["candidates"]
-    if split:
-        assert np.allclose(L0, L5, rtol=1e-6, atol=0)
-    else:
-        assert np.array_equal(L0, L5)
     torch.cuda.synchronize()
