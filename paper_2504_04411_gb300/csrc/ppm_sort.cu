@@ -119,6 +119,7 @@ constexpr int kSpinLimit = 1 << 22;
 constexpr int kStatusHead = 32;          // words before the per-tile words: [0] tile counter
 constexpr int kSweepItems = 8;           // keys a thread in the single-pass kernel
 constexpr int kSweepTile = kSortThreads * kSweepItems;
+constexpr int kLookBack = 4;             // earlier tiles' words a look-back round trip reads
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p)
 {
@@ -224,18 +225,36 @@ k_radix_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ 
             st_relaxed_u64(word + dg, kFlagInclusive | local);
         } else {
             st_relaxed_u64(word + (int64_t)t * 256 + dg, kFlagAggregate | local);
+            // kLookBack earlier tiles' words per round trip, consumed from
+            // the nearest one back to the first INCLUSIVE one or the first
+            // one not yet published (waited for, then read again)
             int q = t - 1, spins = 0;
-            while (q >= 0) {
-                const unsigned long long x = ld_relaxed_u64(word + (int64_t)q * 256 + dg);
-                const unsigned long long f = x & ~kCountMask;
-                if (f == 0ull) {
+            bool found = false;
+            while (!found) {
+                unsigned long long x[kLookBack];
+#pragma unroll
+                for (int i = 0; i < kLookBack; ++i)
+                    x[i] = q - i >= 0 ? ld_relaxed_u64(word + (int64_t)(q - i) * 256 + dg) : kFlagInclusive;
+                int used = 0;
+                bool stop = false;
+#pragma unroll
+                for (int i = 0; i < kLookBack; ++i) {
+                    if (!stop) {
+                        const unsigned long long f = x[i] & ~kCountMask;
+                        if (f == 0ull) {
+                            stop = true;
+                        } else {
+                            excl += x[i] & kCountMask;
+                            ++used;
+                            if (f == kFlagInclusive) stop = found = true;
+                        }
+                    }
+                }
+                q -= used;
+                if (!found && used < kLookBack) {
                     if (++spins > spin_limit) { atomicOr(err, 4); break; }
                     __nanosleep(32);
-                    continue;
                 }
-                excl += x & kCountMask;
-                if (f == kFlagInclusive) break;
-                --q;
             }
             st_relaxed_u64(word + (int64_t)t * 256 + dg, kFlagInclusive | (excl + local));
         }
