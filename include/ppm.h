@@ -97,7 +97,8 @@ typedef struct {
     double alpha_f;     /* significance level alpha_F, 0.01 (Sec. 6.1.1) */
     float k;            /* shrinking ratio of Eq. (radiusupdate), 0.7 (Sec. 6.1.1) */
     float rmin_ratio;   /* r_min = rmin_ratio * r0, 0.001 (Sec. 6.1.2) */
-    float cell_factor;  /* grid cell edge = cell_factor * max radius, in [0.5, 4]; 1 */
+    float cell_factor;  /* grid cell edge = cell_factor * max radius along y and
+                           z (half of it along x), in [0.5, 4]; 1 */
     int32_t channels;   /* flux channels of every iteration: 1 or 3 */
     int32_t rgb_test;   /* 0: F-test on luminance (default); 1: one F-test per
                            RGB channel, reject if any rejects (Sec. 5.1) */
@@ -155,7 +156,8 @@ typedef struct {
     int64_t rejects;       /* hit points whose null hypothesis was rejected */
     int64_t pairs_total;   /* pairs summed over all iterations */
     float r_max;           /* largest radius after the update */
-    float cell;            /* grid cell edge used by the last build */
+    float cell;            /* grid cell edge along y and z used by the last
+                              build (the edge along x is half of it) */
     int32_t launches;      /* kernels launched by the last build + gather */
     float gather_ms;       /* batches: device time of the last gather launch
                               (events recorded around it); contexts: -1 */

@@ -174,16 +174,7 @@ __global__ void k_batch_geom(int P, const float* __restrict__ rmax, const float*
     if (p >= P) return;
     float r = rmax[p];
     if (!(r > 0.f)) r = 1e-30f;
-    const float h = __fmul_rn(cf[p], r);
-    GridGeom g;
-    g.h = h;
-    g.inv_h = __frcp_rn(h);
-    g.tmask = tmask;
-    g.lb = lb;
-    g.pid = (uint32_t)p;
-    g.psimax = 0.f;
-    g.pad[0] = g.pad[1] = 0u;
-    geom[p] = g;
+    geom[p] = ppm_make_geom(__fmul_rn(cf[p], r), tmask, lb, (uint32_t)p);
     // Eq. (radiusupdate) bound r_min sqrt((i+1)^(alpha-1)), FP64 then FP32
     bound[p] = (float)((double)rmin[p] * sc->bound_scale);
     rmax_next[p] = 0.f;
@@ -226,7 +217,7 @@ k_batch_pack(const int4* __restrict__ blocks, const PhotonPtrs* __restrict__ pta
     reinterpret_cast<uint4*>(rec)[S - 1] = make_uint4(pt.nq ? pt.nq[i] : 0u, VCM ? pt.wq[i] : 0u,
                                                       VCM ? __float_as_uint(pt.rho[2ll * i + 1]) : 0u,
                                                       (uint32_t)p);
-    keys[o] = ppm_bucket(ppm_cell_coord(x, g.inv_h), ppm_cell_coord(y, g.inv_h),
+    keys[o] = ppm_bucket(ppm_cell_coord(x, g.inv_hx), ppm_cell_coord(y, g.inv_h),
                          ppm_cell_coord(z, g.inv_h), g);
     vals[o] = (uint32_t)o;
     vmax = NCH == 3 ? fmaxf(fmaxf(psi, R), fmaxf(G, Bc)) : psi;

@@ -230,8 +230,8 @@ __device__ __forceinline__ CellBox cell_box(const Hit& H, const GridGeom& G)
     const float rc = fmaf(H.r, 1.0009765625f,
                           (fabsf(H.P.x) + fabsf(H.P.y) + fabsf(H.P.z) + H.r) * 1.0e-6f);
     CellBox b;
-    b.ix0 = ppm_cell_coord(__fsub_rn(H.P.x, rc), G.inv_h);
-    b.ix1 = ppm_cell_coord(__fadd_rn(H.P.x, rc), G.inv_h);
+    b.ix0 = ppm_cell_coord(__fsub_rn(H.P.x, rc), G.inv_hx);
+    b.ix1 = ppm_cell_coord(__fadd_rn(H.P.x, rc), G.inv_hx);
     b.iy0 = ppm_cell_coord(__fsub_rn(H.P.y, rc), G.inv_h);
     b.iy1 = ppm_cell_coord(__fadd_rn(H.P.y, rc), G.inv_h);
     b.iz0 = ppm_cell_coord(__fsub_rn(H.P.z, rc), G.inv_h);
@@ -285,8 +285,8 @@ __device__ __forceinline__ void row_xrange(const Hit& H, const GridGeom& G, cons
     const float ryz2 = rz2 - gy * gy;
     if (rz2 + rcu.slack < 0.f || ryz2 + rcu.slack < 0.f) return;
     const float half = sqrtf(fmaxf(ryz2, 0.f) + rcu.slack) + rcu.eps;
-    x0 = max(b.ix0, ppm_cell_coord(__fsub_rn(H.P.x, half), G.inv_h));
-    x1 = min(b.ix1, ppm_cell_coord(__fadd_rn(H.P.x, half), G.inv_h));
+    x0 = max(b.ix0, ppm_cell_coord(__fsub_rn(H.P.x, half), G.inv_hx));
+    x1 = min(b.ix1, ppm_cell_coord(__fadd_rn(H.P.x, half), G.inv_hx));
 }
 
 // traversal 0: the thread walks its own cells
@@ -294,13 +294,13 @@ template <int NCH, int NTC, bool NORMALS, bool VCM, bool BATCH, typename SM>
 __device__ void gather_own(const GatherArgs& a, const Hit& H, const GridGeom& G, CellBox b,
                            SM& sm, int tid, Acc<NCH>& acc)
 {
-    const int B = 1 << G.lb;
-    if (b.ix1 - b.ix0 >= B || b.iy1 - b.iy0 >= B || b.iz1 - b.iz0 >= B) {
+    const int B = 1 << G.lb, BX = ppm_block_x(G);
+    if (b.ix1 - b.ix0 >= BX || b.iy1 - b.iy0 >= B || b.iz1 - b.iz0 >= B) {
         // the sphere spans more cells than a block: distinct cells could
         // share a bucket; never happens for r <= max radius and sane
         // coordinates -- flag it instead of double counting
         atomicOr(a.err, 1);
-        b.ix1 = min(b.ix1, b.ix0 + B - 1); b.iy1 = min(b.iy1, b.iy0 + B - 1); b.iz1 = min(b.iz1, b.iz0 + B - 1);
+        b.ix1 = min(b.ix1, b.ix0 + BX - 1); b.iy1 = min(b.iy1, b.iy0 + B - 1); b.iz1 = min(b.iz1, b.iz0 + B - 1);
     }
     const RowCull rcu = row_cull(H, G, b);
     for (int iz = b.iz0; iz <= b.iz1; ++iz) {
@@ -312,11 +312,11 @@ __device__ void gather_own(const GatherArgs& a, const Hit& H, const GridGeom& G,
             const float ryz2 = rz2 - gy * gy;
             if (ryz2 + rcu.slack < 0.f) continue;
             const float half = sqrtf(fmaxf(ryz2, 0.f) + rcu.slack) + rcu.eps;
-            const int xa = max(b.ix0, ppm_cell_coord(__fsub_rn(H.P.x, half), G.inv_h));
-            const int xb = min(b.ix1, ppm_cell_coord(__fadd_rn(H.P.x, half), G.inv_h));
+            const int xa = max(b.ix0, ppm_cell_coord(__fsub_rn(H.P.x, half), G.inv_hx));
+            const int xb = min(b.ix1, ppm_cell_coord(__fadd_rn(H.P.x, half), G.inv_hx));
             int ix = xa;
             while (ix <= xb) {
-                const int ixe = min(xb, ix | (B - 1));          // end of this block's run
+                const int ixe = min(xb, ix | (BX - 1));         // end of this block's run
                 const uint32_t b0 = ppm_bucket(ix, iy, iz, G);
                 const uint32_t s = __ldg(a.cell_start + b0);
                 const uint32_t e = __ldg(a.cell_start + b0 + (uint32_t)(ixe - ix) + 1u);
@@ -698,10 +698,10 @@ __device__ __forceinline__ void gather_warp_hit(const GatherArgs& a, const Hit& 
                                                 Acc<1>& acc)
 {
     static_assert(NTC == 1, "traversal 4 tests one channel");
-    const int B = 1 << G.lb;
-    if (b.ix1 - b.ix0 >= B || b.iy1 - b.iy0 >= B || b.iz1 - b.iz0 >= B) {
+    const int B = 1 << G.lb, BX = ppm_block_x(G);
+    if (b.ix1 - b.ix0 >= BX || b.iy1 - b.iy0 >= B || b.iz1 - b.iz0 >= B) {
         if (lane == 0) atomicOr(a.err, 1);
-        b.ix1 = min(b.ix1, b.ix0 + B - 1); b.iy1 = min(b.iy1, b.iy0 + B - 1); b.iz1 = min(b.iz1, b.iz0 + B - 1);
+        b.ix1 = min(b.ix1, b.ix0 + BX - 1); b.iy1 = min(b.iy1, b.iy0 + B - 1); b.iz1 = min(b.iz1, b.iz0 + B - 1);
     }
     const RowCull rcu = row_cull(Hj, G, b);
     for (int iz = b.iz0; iz <= b.iz1; ++iz) {
@@ -713,11 +713,11 @@ __device__ __forceinline__ void gather_warp_hit(const GatherArgs& a, const Hit& 
             const float ryz2 = rz2 - gy * gy;
             if (ryz2 + rcu.slack < 0.f) continue;
             const float half = sqrtf(fmaxf(ryz2, 0.f) + rcu.slack) + rcu.eps;
-            const int xa = max(b.ix0, ppm_cell_coord(__fsub_rn(Hj.P.x, half), G.inv_h));
-            const int xb = min(b.ix1, ppm_cell_coord(__fadd_rn(Hj.P.x, half), G.inv_h));
+            const int xa = max(b.ix0, ppm_cell_coord(__fsub_rn(Hj.P.x, half), G.inv_hx));
+            const int xb = min(b.ix1, ppm_cell_coord(__fadd_rn(Hj.P.x, half), G.inv_hx));
             int ix = xa;
             while (ix <= xb) {
-                const int ixe = min(xb, ix | (B - 1));
+                const int ixe = min(xb, ix | (BX - 1));
                 const uint32_t b0 = ppm_bucket(ix, iy, iz, G);
                 const uint32_t s = __ldg(a.cell_start + b0);
                 const uint32_t e = __ldg(a.cell_start + b0 + (uint32_t)(ixe - ix) + 1u);
@@ -867,22 +867,22 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
         const int X0 = __reduce_min_sync(full, b.ix0), X1 = __reduce_max_sync(full, b.ix1);
         const int Y0 = __reduce_min_sync(full, b.iy0), Y1 = __reduce_max_sync(full, b.iy1);
         const int Z0 = __reduce_min_sync(full, b.iz0), Z1 = __reduce_max_sync(full, b.iz1);
-        const int B = 1 << G.lb;
+        const int B = 1 << G.lb, BX = ppm_block_x(G);
         const bool any_live = __any_sync(full, live);
-        if (any_live && (X1 - X0 >= B || Y1 - Y0 >= B || Z1 - Z0 >= B)) {
+        if (any_live && (X1 - X0 >= BX || Y1 - Y0 >= B || Z1 - Z0 >= B)) {
             // union wider than a hash block: every lane walks its own cells
             // and queues only its own pairs (its own slots: no conflicts)
             if (live) {
                 int bx1 = b.ix1, by1 = b.iy1, bz1 = b.iz1;
-                if (b.ix1 - b.ix0 >= B || b.iy1 - b.iy0 >= B || b.iz1 - b.iz0 >= B) {
+                if (b.ix1 - b.ix0 >= BX || b.iy1 - b.iy0 >= B || b.iz1 - b.iz0 >= B) {
                     atomicOr(a.err, 1);
-                    bx1 = min(bx1, b.ix0 + B - 1); by1 = min(by1, b.iy0 + B - 1); bz1 = min(bz1, b.iz0 + B - 1);
+                    bx1 = min(bx1, b.ix0 + BX - 1); by1 = min(by1, b.iy0 + B - 1); bz1 = min(bz1, b.iz0 + B - 1);
                 }
                 for (int iz = b.iz0; iz <= bz1; ++iz)
                     for (int iy = b.iy0; iy <= by1; ++iy) {
                         int ix = b.ix0;
                         while (ix <= bx1) {
-                            const int ixe = min(bx1, ix | (B - 1));
+                            const int ixe = min(bx1, ix | (BX - 1));
                             const uint32_t b0 = ppm_bucket(ix, iy, iz, G);
                             const uint32_t s = __ldg(a.cell_start + b0);
                             const uint32_t e = __ldg(a.cell_start + b0 + (uint32_t)(ixe - ix) + 1u);
@@ -910,7 +910,7 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
                     const int rx1 = __reduce_max_sync(full, need ? tx1 : INT_MIN);
                     int ix = rx0;
                     while (ix <= rx1) {
-                        const int ixe = min(rx1, ix | (B - 1));
+                        const int ixe = min(rx1, ix | (BX - 1));
                         const uint32_t b0 = ppm_bucket(ix, iy, iz, G);
                         const uint32_t s = __ldg(a.cell_start + b0);
                         const uint32_t e = __ldg(a.cell_start + b0 + (uint32_t)(ixe - ix) + 1u);
@@ -953,9 +953,9 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
         const int X0 = __reduce_min_sync(full, b.ix0), X1 = __reduce_max_sync(full, b.ix1);
         const int Y0 = __reduce_min_sync(full, b.iy0), Y1 = __reduce_max_sync(full, b.iy1);
         const int Z0 = __reduce_min_sync(full, b.iz0), Z1 = __reduce_max_sync(full, b.iz1);
-        const int B = 1 << G.lb;
+        const int B = 1 << G.lb, BX = ppm_block_x(G);
         const bool any_live = __any_sync(full, live);
-        if (any_live && (X1 - X0 >= B || Y1 - Y0 >= B || Z1 - Z0 >= B)) {
+        if (any_live && (X1 - X0 >= BX || Y1 - Y0 >= B || Z1 - Z0 >= B)) {
             // union wider than a hash block: walk per lane instead
             if (live) gather_own<NCH, NTC, NORMALS, VCM, BATCH>(a, H, G, b, sm, tid, acc);
         } else if (any_live) {
@@ -971,7 +971,7 @@ __device__ __forceinline__ void gather_block(const GatherArgs& a, const Prob& pr
                     const int rx1 = __reduce_max_sync(full, need ? tx1 : INT_MIN);
                     int ix = rx0;
                     while (ix <= rx1) {
-                        const int ixe = min(rx1, ix | (B - 1));
+                        const int ixe = min(rx1, ix | (BX - 1));
                         const uint32_t b0 = ppm_bucket(ix, iy, iz, G);
                         const uint32_t s = __ldg(a.cell_start + b0);
                         const uint32_t e = __ldg(a.cell_start + b0 + (uint32_t)(ixe - ix) + 1u);

@@ -19,16 +19,7 @@ __global__ void k_grid_geom(GridGeom* __restrict__ g, const float* __restrict__ 
 {
     float r = *rmax;
     if (!(r > 0.f)) r = 1e-30f;
-    const float h = __fmul_rn(cell_factor, r);
-    GridGeom o;
-    o.h = h;
-    o.inv_h = __frcp_rn(h);
-    o.tmask = tmask;
-    o.lb = lb;
-    o.pid = 0u;
-    o.psimax = 0.f;
-    o.pad[0] = o.pad[1] = 0u;
-    *g = o;
+    *g = ppm_make_geom(__fmul_rn(cell_factor, r), tmask, lb, 0u);
 }
 
 // Rec. 709 luminance of an RGB flux (the paper tests luminance, Sec. 5.1).
@@ -85,7 +76,7 @@ k_pack_keys(int64_t n, const float* __restrict__ pos, const float* __restrict__ 
     if constexpr (AUX)
         reinterpret_cast<uint4*>(rec)[S - 1] = make_uint4(nq ? nq[i] : 0u, VCM ? wq[i] : 0u,
                                                           VCM ? __float_as_uint(rho[2 * i + 1]) : 0u, 0u);
-    const int ix = ppm_cell_coord(x, g.inv_h);
+    const int ix = ppm_cell_coord(x, g.inv_hx);
     const int iy = ppm_cell_coord(y, g.inv_h);
     const int iz = ppm_cell_coord(z, g.inv_h);
     keys[i] = ppm_bucket(ix, iy, iz, g);
@@ -199,17 +190,18 @@ int reserve_photons(ppm_ctx* c, int64_t n)
 // 4 blocks of B^3 cells.
 int ppm_table_bits(int64_t n, int lb)
 {
-    // at least 2 buckets a photon; then up to 8 while the keys need no
+    // at least 2 buckets a photon per cell of a cubic grid (2^sx in all);
+    // then up to 8 (2^(sx+3)) while the keys need no
     // further 8-bit radix pass and the table stays within 2^29 entries
     // (2 GB): with more buckets fewer hash blocks share a bucket range, so
     // fewer photons of other cells are tested (2M photons: 2^22 -> 2^24
     // buckets, 8% fewer candidates; 16M photons: 2^25 -> 2^27, 8% fewer,
     // gather 5% faster, the build unchanged at four passes; 53M photons:
     // 2^27 -> 2^29, gather 20.2 -> 19.7 ms)
-    int b = 3 * lb + 2;
-    while (b < 30 && ((int64_t)1 << b) < 2 * n) ++b;
+    int b = 3 * lb + kXSplit + 2;
+    while (b < 30 && ((int64_t)1 << b) < (2 * n << kXSplit)) ++b;
     const int cap = (b + 7) / 8 * 8 < 29 ? (b + 7) / 8 * 8 : 29;
-    while (b < cap && ((int64_t)1 << b) < 8 * n) ++b;
+    while (b < cap && ((int64_t)1 << b) < (8 * n << kXSplit)) ++b;
     return b;
 }
 

@@ -37,25 +37,51 @@ inline int ppm_flags_status(int32_t flags)
 }
 
 // ---------------------------------------------------------------------------
-// Grid: a uniform grid of cell edge h, hashed into T = 2^tbits buckets.
-// Cells are grouped in blocks of B^3 (B = 2^lb); the low 3*lb bits of a
-// bucket are the cell's coordinates inside its block, the high bits a hash
-// of the block coordinates.  Two consequences the gather relies on:
-//   * distinct cells less than B apart along every axis never share a
-//     bucket, so a hit point whose sphere spans <= B cells per axis visits
-//     each bucket at most once (no duplicate gathering);
+// Grid: a uniform grid of cell edge h along y and z and h / 2^sx along x
+// (kXSplit = sx), hashed into T = 2^tbits buckets.  A row of cells along x
+// is what the gather walks and trims to the sphere's chord, so the finer x
+// edge cuts the photons tested at the row ends without adding rows.  Cells
+// are grouped in blocks of Bx x B x B (B = 2^lb, Bx = 2^(lb + sx), the same
+// extent B h along every axis); the low bits of a bucket are the cell's
+// coordinates inside its block, the high bits a hash of the block
+// coordinates.  Two consequences the gather relies on:
+//   * distinct cells less than a block apart along every axis never share
+//     a bucket, so a hit point whose sphere spans <= Bx cells along x and
+//     <= B along y and z visits each bucket at most once (no duplicate
+//     gathering);
 //   * cells consecutive along x inside one block have consecutive buckets,
 //     so a run of them is one contiguous range of the sorted photons.
 // ---------------------------------------------------------------------------
+constexpr int kXSplit = 1;
+
 struct GridGeom {
-    float inv_h;       // 1 / cell edge
-    float h;           // cell edge
+    float inv_h;       // 1 / cell edge along y and z
+    float h;           // cell edge along y and z
     uint32_t tmask;    // T - 1
-    int32_t lb;        // log2 of the block edge in cells (2 or 3)
+    int32_t lb;        // log2 of the block edge in cells along y and z (2 or 3)
     uint32_t pid;      // problem id mixed into the hash (0 for one problem)
     float psimax;      // largest tested value psi of the grid's photons (>= 0)
-    uint32_t pad[2];
+    float inv_hx;      // 1 / cell edge along x (2^sx / h)
+    int32_t sx;        // log2 of the x split
 };
+
+// cells a block spans along x
+__device__ __forceinline__ int ppm_block_x(const GridGeom& g) { return 1 << (g.lb + g.sx); }
+
+// the geometry of a cell edge h (both grid builders fill it the same way)
+__device__ __forceinline__ GridGeom ppm_make_geom(float h, uint32_t tmask, int lb, uint32_t pid)
+{
+    GridGeom o;
+    o.h = h;
+    o.inv_h = __frcp_rn(h);
+    o.tmask = tmask;
+    o.lb = lb;
+    o.pid = pid;
+    o.psimax = 0.f;
+    o.sx = kXSplit;
+    o.inv_hx = __frcp_rn(__fmul_rn(h, 1.0f / (float)(1 << kXSplit)));
+    return o;
+}
 
 __device__ __forceinline__ uint32_t ppm_fmix32(uint32_t x)
 {
@@ -75,13 +101,13 @@ __device__ __forceinline__ int ppm_cell_coord(float p, float inv_h)
 
 __device__ __forceinline__ uint32_t ppm_bucket(int ix, int iy, int iz, const GridGeom& g)
 {
-    const int lb = g.lb;
-    const uint32_t m = (1u << lb) - 1u;
-    uint32_t local = ((uint32_t)ix & m) | (((uint32_t)iy & m) << lb) | (((uint32_t)iz & m) << (2 * lb));
-    uint32_t bx = (uint32_t)(ix >> lb), by = (uint32_t)(iy >> lb), bz = (uint32_t)(iz >> lb);
+    const int lb = g.lb, lx = g.lb + g.sx;
+    const uint32_t m = (1u << lb) - 1u, mx = (1u << lx) - 1u;
+    uint32_t local = ((uint32_t)ix & mx) | (((uint32_t)iy & m) << lx) | (((uint32_t)iz & m) << (lx + lb));
+    uint32_t bx = (uint32_t)(ix >> lx), by = (uint32_t)(iy >> lb), bz = (uint32_t)(iz >> lb);
     uint32_t hb = ppm_fmix32(bx * 0x9E3779B1u ^ ppm_fmix32(by * 0x85EBCA77u ^
                               ppm_fmix32(bz + 0x27D4EB2Fu + g.pid * 0x632BE59Bu)));
-    return ((hb << (3 * lb)) | local) & g.tmask;
+    return ((hb << (lx + 2 * lb)) | local) & g.tmask;
 }
 
 // Photon records in cell order.  rec0 = (x, y, z, psi) where psi is the
