@@ -359,6 +359,38 @@ def test_exact_boundary_photons(mapping):
     compare(states, stats, L, ref, 1)
 
 
+@pytest.mark.parametrize("mapping", MAPPINGS)
+def test_photons_on_cell_boundaries(mapping):
+    """Photons on a lattice of step 1/64 with cells of edge 0.25 (0.125 along
+    x, the split edge): many photons lie exactly on cell faces along every
+    axis, on the half-cell faces along x, and exactly on disk edges.  Row
+    trimming and the split x cells must keep every in-disk photon: counts
+    equal the oracle's exactly for every traversal."""
+    import torch
+    centres = [(0.5, 0.5), (0.375, 0.625), (0.7, 0.25), (0.123, 0.871), (0.9375, 0.0625)]
+    hp = synth.HitPoints(torch.tensor([[x, y, 0.0] for x, y in centres], dtype=torch.float32).cuda(),
+                         torch.tensor([[1.0, 0.0, 0.0]] * len(centres)).cuda(),
+                         torch.tensor([[0.0, 1.0, 0.0]] * len(centres)).cuda(), None, None)
+    c = np.arange(65, dtype=np.float64) / 64.0
+    xx, yy = np.meshgrid(c, c, indexing="ij")
+    pos = np.stack([xx.ravel(), yy.ravel(), np.zeros(xx.size)], 1).astype(np.float32)
+    J = pos.shape[0]
+    ph = synth.Photons(torch.from_numpy(pos).cuda(), torch.full((J,), 1.0 / J, dtype=torch.float32).cuda(),
+                       None, None, None)
+    params = _params(mapping=mapping, cell_factor=1.0, alpha_f=1e-12)   # cell edge 0.25 = r0
+    states, stats, L = run_gpu(hp, [ph], 0.25, params=params)
+    assert stats[0]["cell"] == pytest.approx(0.25)
+    ref = O.run(hp.numpy(), synth.stack_numpy([ph]), 0.25, 1, alpha_f=1e-12)
+    # the tested counts of the iteration sum to its pairs; a hit point the
+    # test kept holds them as its window (a rejected one starts a new one:
+    # the disks cut by the lattice's edge are far from uniform)
+    assert stats[0]["pairs"] == int(ref.counts[0].sum())
+    kept = states[0]["t"] > 0
+    assert kept.sum() >= 2
+    assert np.array_equal(states[0]["counts"][kept], ref.counts[0][kept].astype(np.int32))
+    compare(states, stats, L, ref, 1)
+
+
 # ------------------------------------------------------------ edge cases ---
 def test_empty_iterations_and_single_hit_point():
     import torch
