@@ -191,16 +191,19 @@ int reserve_photons(ppm_ctx* c, int64_t n)
 int ppm_table_bits(int64_t n, int lb)
 {
     // at least 2 buckets a photon per cell of a cubic grid (2^sx in all);
-    // then up to 8 (2^(sx+3)) while the keys need no
-    // further 8-bit radix pass and the table stays within 2^29 entries
-    // (2 GB): with more buckets fewer hash blocks share a bucket range, so
-    // fewer photons of other cells are tested (2M photons: 2^22 -> 2^24
-    // buckets, 8% fewer candidates; 16M photons: 2^25 -> 2^27, 8% fewer,
-    // gather 5% faster, the build unchanged at four passes; 53M photons:
-    // 2^27 -> 2^29, gather 20.2 -> 19.7 ms)
+    // then up to 8 (2^(sx+3)) while the keys need no further 8-bit radix
+    // pass, or up to 2^25 entries in any case, and the table stays within
+    // 2^29 entries (2 GB): with more buckets fewer hash blocks share a
+    // bucket range, so fewer photons of other cells are tested (2M photons:
+    // 2^22 -> 2^24 buckets, 8% fewer candidates, and with cells split along
+    // x 2^24 -> 2^25, gather -0.10 ms for +0.04 ms of a fourth pass; 16M
+    // photons: 2^25 -> 2^27, 8% fewer, gather 5% faster, the build
+    // unchanged at four passes; 53M photons: 2^27 -> 2^29, gather 20.2 ->
+    // 19.7 ms)
     int b = 3 * lb + kXSplit + 2;
     while (b < 30 && ((int64_t)1 << b) < (2 * n << kXSplit)) ++b;
-    const int cap = (b + 7) / 8 * 8 < 29 ? (b + 7) / 8 * 8 : 29;
+    const int pass_cap = (b + 7) / 8 * 8 > 25 ? (b + 7) / 8 * 8 : 25;
+    const int cap = pass_cap < 29 ? pass_cap : 29;
     while (b < cap && ((int64_t)1 << b) < (8 * n << kXSplit)) ++b;
     return b;
 }
