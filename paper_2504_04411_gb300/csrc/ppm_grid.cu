@@ -1,8 +1,9 @@
 // ppm_grid.cu -- photon map of one iteration (the range-search structure
 // over the light vertices that Sec. 5.1 builds first): a hashed uniform grid.
 //
-//   k_grid_geom  : cell edge h = cell_factor * max_h r_h, read from device
-//                  memory written by the previous update (no host sync);
+//   k_grid_geom  : cell edge h = cell_factor * max_h r_h along y and z,
+//                  h / 2^kXSplit along x, from device memory written by the
+//                  previous update (no host sync);
 //   k_pack_keys  : one coalesced pass over the caller's photons: bucket key,
 //                  identity index, and the photon's 16-byte records side by
 //                  side;
@@ -185,9 +186,8 @@ int reserve_photons(ppm_ctx* c, int64_t n)
 
 }  // namespace
 
-// Bucket-table size: T = 2^tbits >= 2 n (so an empty cell lands on an
-// occupied bucket with probability <= 1/2 per photon-bucket), and at least
-// 4 blocks of B^3 cells.
+// Bucket-table size: T = 2^tbits >= 2 n 2^kXSplit (two buckets a photon
+// per cell of the unsplit grid), and at least 4 blocks of Bx * B^2 cells.
 int ppm_table_bits(int64_t n, int lb)
 {
     // at least 2 buckets a photon per cell of a cubic grid (2^sx in all);
