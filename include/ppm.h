@@ -402,8 +402,8 @@ const char* ppm_strerror(int code);
  *   - n > PPM_NOALLOC_MAX_PAIRS returns PPM_EINVAL (use ppm_sort_pairs).
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current and keeps it for the
- *     life of the process: cudaDeviceReset after that first call is not
- *     supported.
+ *     life of the process: make that first call before any stream capture,
+ *     and cudaDeviceReset after it is not supported.
  *   - All calls share the array: calls whose work overlaps on the GPU
  *     (several streams or host threads on one device) race on it; order
  *     them on one stream.  It keeps the last call's contents; nothing in it

@@ -12,9 +12,10 @@
 //
 // In host code the array's name only stands for the symbol; its device
 // address is obtained once per device with cudaGetSymbolAddress while that
-// device is current (the first call on a device does this set-up).  The
-// address is cached for the life of the process, so cudaDeviceReset after
-// the first call is not supported (the cached address would be stale).
+// device is current (the first call on a device does this set-up, so that
+// first call should come before any stream capture).  The address is cached
+// for the life of the process, so cudaDeviceReset after the first call is
+// not supported (the cached address would be stale).
 // All calls share the array: calls whose work overlaps on the GPU
 // (different streams, or different host threads on one device) race on
 // it.  Every word of the scratch that a call reads is written earlier in
