@@ -421,6 +421,7 @@ def run_single(args, rank, world, local, dist):
         line["e2e"] = {"value": cnt / secs, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
                        "d2h_bytes_per_step": e2e["d2h"], "steps": e2e["steps"],
                        "rounds": e2e["rounds"], "reported": "median of the rounds",
+                       "round_step_ms": e2e["round_step_ms"],
                        "inputs": "fresh photons per step (iterations after the timed ones), page-locked"}
     est.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -487,16 +488,21 @@ def run_e2e(est, sc, first_iter, K, max_steps=None, rounds=5):
         torch.cuda.synchronize()
         pairs = 0
         t0 = time.perf_counter()
+        marks = []
         for i in range(1, K + 1):
             it = est.step_host(host[i])
             if i > 1:
                 pairs += ppm.ppm_stats_host(est.ctx, it - 1).pairs
+                marks.append(time.perf_counter())
         pairs += ppm.ppm_stats_host(est.ctx, est.it).pairs
         torch.cuda.synchronize()
-        results.append((pairs / (time.perf_counter() - t0), pairs, time.perf_counter() - t0))
-    med = sorted(results)[len(results) // 2]
+        t1 = time.perf_counter()
+        marks.append(t1)
+        steps_ms = [round(1e3 * (b - a), 2) for a, b in zip([t0] + marks[:-1], marks)]
+        results.append((pairs / (t1 - t0), pairs, t1 - t0, steps_ms))
+    med = sorted(results, key=lambda r: r[0])[len(results) // 2]
     return {"pairs": med[1], "seconds": med[2], "h2d": h2d, "d2h": d2h, "steps": K,
-            "rounds": [r[0] for r in results]}
+            "rounds": [r[0] for r in results], "round_step_ms": [r[3] for r in results]}
 
 
 def run_batched(args, rank, world, local, dist):

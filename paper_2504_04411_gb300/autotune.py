@@ -23,7 +23,12 @@ import torch
 
 from . import ppm
 
-CANDIDATES = ((0, 0.5), (0, 0.6), (0, 0.75), (0, 1.0), (1, 0.5), (1, 1.0), (4, 0.5), (4, 1.0))
+# Cell factors 2/k (0.5, 2/3, 1) make a sphere of the largest radius span
+# the same number of cells along each axis for nearly every hit point (2 r / h
+# just above an integer), so the threads of a warp walk boxes of one size;
+# 0.6 and 0.75 trade that for fewer or larger cells.
+CANDIDATES = ((0, 0.5), (0, 0.6), (0, 2.0 / 3.0), (0, 0.75), (0, 1.0), (1, 0.5), (1, 1.0), (4, 0.5),
+              (4, 1.0))
 TILES = (64, 128, 256)       # batch tile sizes (hit points), tried for the best traversal
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 

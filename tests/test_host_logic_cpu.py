@@ -28,8 +28,9 @@ def test_tune_picks_the_fastest_and_caches(tmp_path, monkeypatch):
         class pos:
             shape = (5000, 3)
 
-    fake = {(0, 0.5): 3.0, (0, 0.6): 2.5, (0, 0.75): 2.7, (0, 1.0): 3.3, (1, 0.5): 4.0, (1, 1.0): 4.1,
-            (4, 0.5): 9.0, (4, 1.0): 8.0}
+    fake = {(0, 0.5): 3.0, (0, 0.6): 2.5, (0, 2.0 / 3.0): 2.6, (0, 0.75): 2.7, (0, 1.0): 3.3, (1, 0.5): 4.0,
+            (1, 1.0): 4.1, (4, 0.5): 9.0, (4, 1.0): 8.0}
+    assert set(fake) == set(autotune.CANDIDATES)
     calls = []
 
     def timer(hp, batches, r0, mapping, cell_factor, params=None):
