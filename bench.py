@@ -352,7 +352,7 @@ def run_single(args, rank, world, local, dist):
     if args.mapping is not None and args.cell_factor is not None:
         tuned = {"mapping": args.mapping, "cell_factor": args.cell_factor, "key": "given"}
     else:
-        tuned = autotune.tune(hp, batches[:3], sc.r0, params=params)
+        tuned = autotune.tune(hp, batches[:5], sc.r0, params=params)
     params.mapping, params.cell_factor = tuned["mapping"], tuned["cell_factor"]
     flush = None if args.no_flush else torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
