@@ -58,7 +58,7 @@ struct GridGeom {
     float inv_h;       // 1 / cell edge along y and z
     float h;           // cell edge along y and z
     uint32_t tmask;    // T - 1
-    int32_t lb;        // log2 of the block edge in cells along y and z (2 or 3)
+    int32_t lb;        // log2 of the block edge in cells along y and z (2 to 4)
     uint32_t pid;      // problem id mixed into the hash (0 for one problem)
     float psimax;      // largest tested value psi of the grid's photons (>= 0)
     float inv_hx;      // 1 / cell edge along x (2^sx / h)
