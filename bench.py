@@ -448,10 +448,11 @@ def run_e2e(est, sc, first_iter, K, max_steps=None, rounds=5):
     photons of the next iterations (made on the device), and one untimed
     step runs (on the first round it allocates the context's device slots
     for host-fed photons).  Every page-locked batch is copied to the device
-    once, untimed, before the first round: the first DMA over freshly
-    page-locked memory ran at 48-118 GB/s against a steady 209 GB/s after.
-    Photons are never fed twice: repeated photons would inflate the F
-    statistic and shrink every radius."""
+    once, untimed, before the first round: in one probe the first copy out
+    of each newly page-locked batch ran at 48-118 GB/s against a steady 209
+    GB/s after (another probe saw no such cost).  Each round's step times
+    go into the result.  Photons are never fed twice: repeated photons
+    would inflate the F statistic and shrink every radius."""
     import torch
 
     from paper_2504_04411_gb300 import ppm
