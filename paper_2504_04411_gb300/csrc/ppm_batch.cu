@@ -85,7 +85,7 @@ struct ppm_batch {
     IterScalars *sc_h = nullptr, *sc_d = nullptr;
     // grid
     SortScratch sort;
-    int tbits = 0, lb = 3;
+    int tbits = 0, lb = 4;      // hash blocks 16 cells wide along y and z
     uint32_t* cell_start = nullptr;
     float4 *pack = nullptr, *rec0 = nullptr, *rec1 = nullptr;   // pack: a photon's records side by side
     uint4* aux = nullptr;
